@@ -1,0 +1,464 @@
+"""Benchmark of the parallel reduction on GB300.
+
+Headline (one JSON line on stdout): reduce GB/s and fraction of the HBM roofline
+for the plain fp32 sum over n = 2^28 elements (1 GiB, uniform [-1,1)), inputs
+resident in HBM.  A step is one pr_reduce call (one kernel launch); the input is
+8x larger than L2, so no flush is needed between steps.
+
+Also reported in the same line:
+  e2e          the same metric through pr_reduce_host (pinned host buffer, chunked
+               host->device copies, result read back) per step;
+  roofline     achieved / measured HBM peak of the dominant kernel, per launch;
+  cpu_baseline the CPU oracle (exact fixed-point sum, one host core) on the same data;
+  forms        every op / dtype of the sweep at 2^28, the precision modes, the
+               segmented form (4096 log-uniform segments, autotuned, replayed from a
+               CUDA graph) and forward+backward of [64, 2^20] row reductions.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms]
+
+With N > 1 (launched by torch.distributed.run) every rank reduces its own copy
+of the workload on its own GPU (replicas: the path has no exchange step); the
+time is the maximum over ranks and value counts all ranks' bytes.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_HEAD = 1 << 28
+METRIC = "reduce GB/s & % of HBM peak, n=2^28 fp32 sum; segmented/fwd+bwd vs plain"
+WORKLOAD = "plain fp32 sum, n=2^28 uniform[-1,1) (1 GiB), one scalar out"
+KERNEL_SOURCES = ["common.cuh", "traits.cuh", "kernels.cuh", "inst_f32.cu"]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1710_07358_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(key)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_launches(fn, steps, warmup, stream):
+    """Run fn() warmup + steps times; per-launch CUDA events on `stream`.
+    Returns (total ms of the timed region, mean ms per launch)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(steps):
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    return t0.elapsed_time(t1), sum(per) / len(per)
+
+
+def gbs(nbytes, ms):
+    from paper_1710_07358_gb300.metrics import gbs as _g
+    return _g(nbytes, ms * 1e-3)
+
+
+def cpu_oracle_sum(x):
+    """The oracle's fp32 sum (exact fixed-point accumulation), one host core."""
+    import oracle
+    t = time.perf_counter()
+    oracle.exact_sum(x, "f32")
+    return time.perf_counter() - t
+
+
+# --------------------------------------------------------------------------
+# Secondary forms (all on the same GPU, same run)
+# --------------------------------------------------------------------------
+
+def forms(steps, warmup, peak):
+    import numpy as np
+    import torch
+    from paper_1710_07358_gb300 import pr, synth
+    from paper_1710_07358_gb300.autograd import RowReduce  # noqa: F401  (same kernels as below)
+    st = torch.cuda.current_stream()
+    k = max(3, min(steps, 30))
+    res = {}
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+
+    def plain(name, t, op, **kw):
+        nb = t.numel() * t.element_size()
+        _, per = time_launches(lambda: pr.reduce(t, op, **kw), k, warmup, st)
+        res[name] = {"GB/s": round(gbs(nb, per), 1), "frac": round(gbs(nb, per) / peak, 4),
+                     "us": round(per * 1e3, 2)}
+
+    n = N_HEAD
+    g.manual_seed(synth.config_seed(1))
+    f32 = torch.rand(n, generator=g, device=dev) * 2 - 1
+    for op in ("sum", "max", "min"):
+        plain("f32_%s" % op, f32, op)
+    i32 = torch.randint(-(1 << 20), 1 << 20, (n,), generator=g, device=dev, dtype=torch.int32)
+    for op in ("sum", "max", "min"):
+        plain("i32_%s" % op, i32, op)
+    del i32
+    u32 = torch.randint(-(1 << 31), (1 << 31) - 1, (n,), generator=g, device=dev, dtype=torch.int32).view(torch.uint32)
+    for op in ("and", "or", "xor"):
+        plain("u32_%s" % op, u32, op)
+    del u32
+    f64 = torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 0.002 + 0.999
+    plain("f64_prod", f64, "prod")
+    del f64
+    for dt, name in ((torch.bfloat16, "bf16"), (torch.float16, "f16")):
+        h = torch.randn(n, generator=g, device=dev).to(dt)
+        plain("%s_sum" % name, h, "sum")
+        plain("%s_sum_compensated" % name, h, "sum", precision="compensated")
+        del h
+    plain("f32_sum_compensated", f32, "sum", precision="compensated")
+    plain("f32_sum_fp64_combine", f32, "sum", precision="fp64_combine")
+    del f32
+
+    # precision: ill-conditioned fp32 set, error against the exact sum (known by construction)
+    x, n_big, exact = synth.ill_conditioned_f32(1 << 26, synth.config_seed(2))
+    xt = torch.from_numpy(x).to(dev)
+    abs_sum = float(np.abs(x.astype(np.float64)).sum())
+    errs = {}
+    for prec in ("plain", "fp64_combine", "compensated"):
+        v = pr.reduce(xt, "sum", precision=prec).item()
+        errs[prec] = {"result": v, "abs_err": abs(v - exact), "err_over_sum_abs": abs(v - exact) / abs_sum}
+    plain("f32_illcond_compensated", xt, "sum", precision="compensated")
+    res["illcond_errors"] = {"n": 1 << 26, "exact": exact, "kappa": abs_sum / exact, **errs}
+    del xt
+
+    # segmented: 4096 log-uniform segments, autotuned, replayed from a CUDA graph
+    vals, off = synth.segmented_workload(4096, synth.config_seed(3))
+    xv = torch.from_numpy(vals).to(dev)
+    ov = torch.from_numpy(off).to(dev)
+    seg_bytes = 4 * vals.size + 8 * off.size + 4 * 4096
+    for op in ("sum", "max"):
+        cfg = pr.autotune("segmented", xv, op, offsets=ov)
+        out = torch.empty(4096, dtype=torch.float32, device=dev)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            pr.prepare(s)
+            pr.check(pr.pr_segmented_reduce(xv.data_ptr(), ov.data_ptr(), 4096, 0, pr.OPS[op], out.data_ptr(),
+                                            s.cuda_stream))
+        s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            pr.check(pr.pr_segmented_reduce(xv.data_ptr(), ov.data_ptr(), 4096, 0, pr.OPS[op], out.data_ptr(),
+                                            s.cuda_stream))
+        _, per = time_launches(graph.replay, k, warmup, torch.cuda.current_stream())
+        res["segmented_%s" % op] = {"GB/s": round(gbs(seg_bytes, per), 1), "frac": round(gbs(seg_bytes, per) / peak, 4),
+                                    "us": round(per * 1e3, 2), "elements": int(vals.size), "config": cfg,
+                                    "graph": True}
+    del xv, ov
+
+    # differentiation: [64, 2^20] fp32, forward + backward
+    rows, cols = 64, 1 << 20
+    xr = torch.randn(rows, cols, generator=g, device=dev)
+    xp = torch.rand(rows, cols, generator=g, device=dev) + 0.5
+    xp[torch.rand(rows, cols, generator=g, device=dev) < 0.01] = 0.0
+    go = torch.linspace(-1, 1, rows, device=dev)
+    mat = rows * cols * 4
+    for op in ("sum", "max", "prod"):
+        xin = xp if op == "prod" else xr
+
+        def fwd():
+            if op == "sum":
+                return pr.reduce_rows(xin, op), None
+            if op == "max":
+                return pr.reduce_rows(xin, op, argidx=True)
+            return pr.reduce_rows(xin, op, aux=True)
+
+        y, extra = fwd()
+        gi = torch.empty_like(xin)
+
+        def bwd():
+            if op == "max":
+                pr.reduce_backward(op, xin, go, argidx=extra, out=gi)
+            elif op == "prod":
+                pr.reduce_backward(op, xin, go, aux=extra, out=gi)
+            else:
+                pr.reduce_backward(op, xin, go, out=gi)
+
+        _, pf = time_launches(fwd, k, warmup, st)
+        _, pb = time_launches(bwd, k, warmup, st)
+        res["fwd_bwd_%s" % op] = {"fwd_GB/s": round(gbs(mat, pf), 1), "bwd_GB/s": round(gbs(mat, pb), 1),
+                                  "fwd_bwd_GB/s": round(gbs(2 * mat, pf + pb), 1),
+                                  "frac": round(gbs(2 * mat, pf + pb) / peak, 4),
+                                  "us": round((pf + pb) * 1e3, 2)}
+    return res
+
+
+# --------------------------------------------------------------------------
+# Arms
+# --------------------------------------------------------------------------
+
+def smi_index(local):
+    """nvidia-smi's index of CUDA device `local` (honours CUDA_VISIBLE_DEVICES)."""
+    ids = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    if local < len(ids) and ids[local].isdigit():
+        return int(ids[local])
+    return local
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle on the host cores, same workload and metric (bounded sample per step)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1710_07358_gb300 import synth
+    oracle.build()
+    x = synth.uniform_f32(N_HEAD, synth.config_seed(1))
+    # size each step's sample so that warmup + steps take about two minutes
+    probe = x[: 1 << 20]
+    t = time.perf_counter()
+    oracle.exact_sum(probe, "f32")
+    per_elem = max((time.perf_counter() - t) / probe.size, 1e-10)
+    total = max(args.steps + args.warmup, 1)
+    m = int(min(N_HEAD, max(1 << 16, 120.0 / total / per_elem)))
+    sample = x[:m]
+    for _ in range(args.warmup):
+        oracle.exact_sum(sample, "f32")
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.exact_sum(sample, "f32")
+    dt = (time.perf_counter() - t) / max(args.steps, 1)
+    v = gbs(m * 4, dt * 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_HEAD, "op": "sum", "dtype": "f32",
+                                           "parallelism": "replicas"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "first %d elements of the n=2^28 workload per step" % m},
+            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1710_07358_gb300 import pr, synth
+    peak, peak_src = measured_peaks()
+
+    x_host = synth.uniform_f32(N_HEAD, synth.config_seed(1))
+    x = torch.from_numpy(x_host).to(dev)
+    out = torch.empty((), dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    nbytes = N_HEAD * 4
+
+    def step():
+        pr.reduce(x, "sum", out=out)
+
+    sampler = ClockSampler(smi_index(dev.index))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    total_ms, per_launch = time_launches(step, args.steps, 0, st)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    value = gbs(nbytes * world, ms_per_step)
+
+    # correctness of the timed result (exactness bound) on rank 0
+    res_val = out.item()
+
+    # end to end: pinned host buffer through the C ABI
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.from_numpy(x_host).pin_memory()
+        ke = max(3, min(args.steps, 10))
+        pr.reduce_host(pinned, "sum")
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t = time.perf_counter()
+        for _ in range(ke):
+            pr.reduce_host(pinned, "sum")
+        e2e_s = time.perf_counter() - t
+        if world > 1:
+            tt = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = tt.item()
+        e2e_s /= ke
+        e2e = {"value": round(gbs(nbytes * world, e2e_s * 1e3), 1), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": 4, "steps": ke}
+
+    achieved = gbs(nbytes, per_launch)
+    cfg = pr.get_config("reduce", "f32", "sum", "plain", N_HEAD)
+    traffic = traffic_for("reduce_f32_sum_2^28")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy)",
+                "kernel": "k_reduce<SumF<LdF32,float>,U=%d,VB=%d>" % (cfg["unroll"], cfg["vec_bytes"]),
+                "algorithmic_bytes_per_launch": nbytes, "launch_us": round(per_launch * 1e3, 2)}
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_HEAD, "op": "sum", "dtype": "f32",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "input 1 GiB > 129 MB L2; no flush needed", "launch": cfg},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
+            "result": res_val}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt = cpu_oracle_sum(x_host)
+        line["cpu_baseline"] = {"value": round(gbs(nbytes, dt * 1e3), 4), "unit": "GB/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "whole n=2^28 workload once (exact fixed-point sum, one core)"}
+        import oracle
+        line["abs_err_vs_exact"] = oracle.sum_error(x_host, "f32", res_val)
+        line["err_bound_1e-6_sum_abs"] = 1e-6 * oracle.abs_sum(x_host, "f32")
+    if rank == 0 and world == 1 and not args.no_forms:
+        del x
+        torch.cuda.empty_cache()
+        line["forms"] = forms(args.steps, args.warmup, peak)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-log2", type=int, default=28,
+                    help="headline size 2^k (28 is the measured workload; smaller only for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    global N_HEAD, WORKLOAD
+    if args.n_log2 != 28:
+        N_HEAD = 1 << args.n_log2
+        WORKLOAD = "plain fp32 sum, n=2^%d uniform[-1,1) (profiling case, not the measured workload)" % args.n_log2
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

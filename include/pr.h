@@ -1,0 +1,229 @@
+/*
+ * pr.h -- C ABI of the GB300 (sm_103a) parallel-reduction library libpr.so.
+ *
+ * A reduction computes x_0 (x) x_1 (x) ... (x) x_{n-1} for an associative
+ * combiner (x) (Section 1.1, "Problem Definition").  The library implements it
+ * as one persistent kernel launch per call: grid-stride vector loads into
+ * several independent per-thread accumulators (the loop unrolling of
+ * Section 3, "Unrolling the step 1", on the persistent grid of Section 2.5),
+ * warp and block combines (Sections 2.2-2.3), and the second stage of the
+ * two-stage scheme (Section 2.3) fused into the same launch by a
+ * last-block-done counter, combined in a fixed order so that results are
+ * bitwise identical from run to run for a given launch configuration.
+ *
+ * Conventions for every entry point:
+ *   - Data pointers (x, offsets, out, argidx, aux, grad_*) are DEVICE memory
+ *     owned by the caller, except where a name says "host".  Nothing is freed
+ *     or retained by the library.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) on the CURRENT device.  No host synchronisation
+ *     happens unless stated.
+ *   - The library owns a small workspace per (device, stream): block partials,
+ *     completion counters and an error word.  It is created on the first call
+ *     for that pair, or by pr_prepare(); after that, calls allocate nothing and
+ *     may be captured into a CUDA graph.  A first call made while the stream is
+ *     capturing fails with PR_ERR_INVALID.  Calls issued concurrently on ONE
+ *     stream from several host threads are serialised by the stream itself.
+ *   - Arguments are validated on the host before anything is enqueued: a
+ *     non-OK status means nothing was launched.  pr_last_error_message() gives
+ *     the reason.  Asynchronous device-side errors are reported by
+ *     pr_last_device_error().
+ *   - Integer / bitwise / max / min results are exact (bit-identical to the
+ *     sequential loop).  Floating-point sums and products depend on the
+ *     association order (Section 1.1, footnote on reordering); for a fixed
+ *     configuration (pr_config) the order, and so the result, is fixed.
+ *
+ * Result types (pr_out_dtype):
+ *   F32 -> F32;  F16/BF16: SUM,PROD -> F32, MAX,MIN -> same type;  F64 -> F64;
+ *   I32: SUM -> I64 (exact), others -> I32 (PROD wraps mod 2^32);
+ *   U32 -> U32 (SUM, PROD wrap mod 2^32);  I64 -> I64 (SUM, PROD wrap mod 2^64).
+ *   AND/OR/XOR are defined on integer types only (PR_ERR_UNSUPPORTED on floats).
+ * Empty input (n == 0, or an empty segment) yields the identity: SUM 0, PROD 1,
+ * MAX -inf / INT_MIN / 0, MIN +inf / INT_MAX / UINT_MAX, AND all ones, OR/XOR 0.
+ * Float MAX/MIN propagate NaN and order -0 below +0.
+ */
+#ifndef PR_H
+#define PR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* pr_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    PR_F32 = 0, PR_F16 = 1, PR_BF16 = 2, PR_F64 = 3, PR_I32 = 4, PR_U32 = 5, PR_I64 = 6
+} pr_dtype;
+
+/* The combiners of Section 1.1 (set intersection / union are AND / OR on
+ * bitset words). */
+typedef enum {
+    PR_SUM = 0, PR_PROD = 1, PR_MAX = 2, PR_MIN = 3, PR_AND = 4, PR_OR = 5, PR_XOR = 6
+} pr_op;
+
+typedef enum {
+    PR_OK = 0,
+    PR_ERR_INVALID = 1,      /* bad pointer / size / enum / state */
+    PR_ERR_UNSUPPORTED = 2,  /* (dtype, op, precision) combination not defined */
+    PR_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    PR_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
+    PR_ERR_NOMEM = 5         /* workspace allocation failed */
+} pr_status;
+
+/* Precision of floating-point SUM (Section 1.1, second footnote: use double
+ * precision or Kahan-style compensation to cut the accumulated error).
+ *   PLAIN          per-thread fp32 accumulators, fp32 combines (fp64 input: fp64).
+ *   COMPENSATED    per-thread Neumaier (sum, compensation) pairs in fp32, combined
+ *                  across threads and blocks in fp64 Neumaier, rounded once.
+ *   FP64_COMBINE   per-thread fp32 accumulators, fp64 warp/block/grid combine. */
+typedef enum {
+    PR_PREC_PLAIN = 0, PR_PREC_COMPENSATED = 1, PR_PREC_FP64_COMBINE = 2
+} pr_precision;
+
+/* Launch configuration of one kernel family (chosen by the autotuner).
+ *   block          threads per block (multiple of 32, 64..1024)
+ *   blocks_per_sm  persistent blocks per SM (clamped to the occupancy limit)
+ *   unroll         independent accumulators / vectors in flight per thread (1,2,4,8)
+ *   vec_bytes      bytes per vector load (16 or 32) */
+typedef struct {
+    int32_t block;
+    int32_t blocks_per_sm;
+    int32_t unroll;
+    int32_t vec_bytes;
+} pr_config;
+
+typedef enum { PR_KIND_REDUCE = 0, PR_KIND_SEGMENTED = 1, PR_KIND_BACKWARD = 2 } pr_kind;
+
+/* Per-segment state that the product's gradient needs. */
+typedef struct {
+    double p_nz;          /* product of the non-zero elements (as double) */
+    int64_t zero_count;   /* number of elements equal to +-0 */
+    int64_t first_zero;   /* index (within the segment) of the first zero, -1 if none */
+} pr_prod_aux;
+
+/* ---------------------------------------------------------------------- */
+/* Plain reduction                                                          */
+/* ---------------------------------------------------------------------- */
+
+/* out[0] = x[0] (x) ... (x) x[n-1]                (Section 1.1; Sections 2.3, 3)
+ * x: n elements of `dtype` (any alignment of the element type).  n >= 0;
+ * x may be NULL only if n == 0.  out: one element of pr_out_dtype(dtype, op). */
+pr_status pr_reduce(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* out,
+                    pr_stream_t stream);
+
+/* As pr_reduce, with a precision mode for float SUM and a choice of output
+ * type: out_dtype is pr_out_dtype(dtype, op), or PR_F64 for a float SUM under
+ * COMPENSATED / FP64_COMBINE (the fp64 combined value, before the final
+ * rounding).  Non-PLAIN precision with any other (dtype, op):
+ * PR_ERR_UNSUPPORTED.                          (Section 1.1, second footnote) */
+pr_status pr_reduce_ex(const void* x, int64_t n, pr_dtype dtype, pr_op op,
+                       pr_precision precision, pr_dtype out_dtype, void* out,
+                       pr_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Segmented reduction: many independent reductions in one launch           */
+/* ---------------------------------------------------------------------- */
+
+/* out[s] = reduction of x[offsets[s] .. offsets[s+1]) for s in [0, nseg).
+ * offsets: nseg+1 int64 in device memory, non-decreasing, offsets[0] >= 0 and
+ * offsets[nseg] <= the length of x (the caller's contract; checked on the
+ * device, a violation sets PR_ERR_INVALID in the device error word and the
+ * affected outputs are unspecified).  nseg >= 0.  out: nseg elements of
+ * pr_out_dtype(dtype, op).  Empty segments get the identity.
+ * The result of each segment is independent of the others' lengths only up to
+ * float association order, which is fixed for a fixed configuration.
+ *                                             (Section 1.1 applied per segment) */
+pr_status pr_segmented_reduce(const void* x, const int64_t* offsets, int64_t nseg,
+                              pr_dtype dtype, pr_op op, void* out, pr_stream_t stream);
+
+/* As pr_segmented_reduce, plus optional outputs (pass NULL to skip):
+ *   argidx (MAX/MIN only): int64 per segment, index WITHIN the segment of the
+ *           first element attaining the extremum (-1 for an empty segment);
+ *   aux (PROD, F32/F64 only): pr_prod_aux per segment.
+ * precision applies to float SUM as in pr_reduce_ex (out type unchanged). */
+pr_status pr_segmented_reduce_aux(const void* x, const int64_t* offsets, int64_t nseg,
+                                  pr_dtype dtype, pr_op op, pr_precision precision,
+                                  void* out, int64_t* argidx, pr_prod_aux* aux,
+                                  pr_stream_t stream);
+
+/* Row reduction of a contiguous row-major [rows, cols] array along its last
+ * dimension: segments of equal length without an offsets array.  Outputs as in
+ * pr_segmented_reduce_aux, one per row.  rows, cols >= 0. */
+pr_status pr_reduce_rows(const void* x, int64_t rows, int64_t cols, pr_dtype dtype, pr_op op,
+                         pr_precision precision, void* out, int64_t* argidx,
+                         pr_prod_aux* aux, pr_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Differentiation of a row reduction (F32 and F64)                         */
+/* ---------------------------------------------------------------------- */
+
+/* grad_in[r, c] = d out[r] / d x[r, c] * grad_out[r]  for a [rows, cols] x:
+ *   SUM:      grad_out[r]
+ *   MAX/MIN:  grad_out[r] at c == argidx[r] (first arg-extremum), 0 elsewhere
+ *   PROD:     zero_count 0: grad_out[r] * p_nz[r] / x[r,c];
+ *             zero_count 1: grad_out[r] * p_nz[r] at c == first_zero, 0 elsewhere;
+ *             zero_count >= 2: 0
+ * x is read only for PROD (may be NULL otherwise); argidx only for MAX/MIN;
+ * aux only for PROD (both from pr_reduce_rows).  grad_out: rows elements,
+ * grad_in: rows*cols elements, both of `dtype`. */
+pr_status pr_reduce_backward(pr_op op, pr_dtype dtype, const void* x, int64_t rows, int64_t cols,
+                             const void* grad_out, const int64_t* argidx,
+                             const pr_prod_aux* aux, void* grad_in, pr_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* End to end from host memory                                              */
+/* ---------------------------------------------------------------------- */
+
+/* host_out[0] = reduction of host_x[0..n): the input is streamed to the device
+ * in chunks (copies overlapped with the reduction of the previous chunk) and
+ * the result copied back; returns after host_out is written.  host_x should be
+ * pinned (cudaHostAlloc / cudaHostRegister) for full copy bandwidth.  Chunk
+ * partials are combined in chunk order, so the result is deterministic for a
+ * fixed n, but a float SUM may differ in the last bits from pr_reduce. */
+pr_status pr_reduce_host(const void* host_x, int64_t n, pr_dtype dtype, pr_op op,
+                         void* host_out, pr_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Set-up, status and tuning                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Create the workspace for (current device, stream) now, so that later calls
+ * on that stream allocate nothing (e.g. before CUDA-graph capture). */
+pr_status pr_prepare(pr_stream_t stream);
+
+/* Synchronise `stream`, read and clear its device error word.  *code receives
+ * the status recorded by a kernel (PR_OK if none). */
+pr_status pr_last_device_error(pr_stream_t stream, int32_t* code);
+
+pr_dtype pr_out_dtype(pr_dtype dtype, pr_op op);
+const char* pr_status_string(pr_status status);
+/* Detail of the last non-OK status returned on the calling host thread. */
+const char* pr_last_error_message(void);
+const char* pr_version(void);
+
+/* Configuration used for (kind, dtype, op, precision, n): the tuned entry for
+ * n's power-of-two bucket if one exists, else the built-in default. */
+pr_status pr_get_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision precision,
+                        int64_t n, pr_config* cfg);
+/* Override the configuration for n's bucket (validated; see pr_config). */
+pr_status pr_set_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision precision,
+                        int64_t n, const pr_config* cfg);
+/* Time every candidate configuration on the caller's data (x, n; offsets and
+ * nseg for PR_KIND_SEGMENTED, else NULL/0) with CUDA events on `stream`, keep
+ * the fastest for n's bucket and return it in *best (may be NULL).  Blocks the
+ * host; must not be called during graph capture.  Writes into the library's
+ * workspace only. */
+pr_status pr_autotune(pr_kind kind, const void* x, int64_t n, const int64_t* offsets,
+                      int64_t nseg, pr_dtype dtype, pr_op op, pr_precision precision,
+                      pr_stream_t stream, pr_config* best);
+/* Persist / restore the tuned table (a small JSON file, keyed by GPU name). */
+pr_status pr_tune_save(const char* path);
+pr_status pr_tune_load(const char* path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PR_H */

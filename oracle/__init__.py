@@ -38,12 +38,21 @@ _NP_STORAGE = {"f32": np.float32, "f16": np.uint16, "bf16": np.uint16, "f64": np
 
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so next to it (gcc, ISO C, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC) or _foreign(_LIB):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
                                _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def _foreign(path):
+    """True if path is an ELF shared object for another CPU architecture."""
+    import platform
+    want = {"x86_64": 62, "aarch64": 183}.get(platform.machine())
+    with open(path, "rb") as f:
+        head = f.read(20)
+    return want is not None and head[:4] == b"\x7fELF" and int.from_bytes(head[18:20], "little") != want
 
 
 _lib = None

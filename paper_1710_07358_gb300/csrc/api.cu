@@ -1,0 +1,719 @@
+// C ABI of libpr.so (declared in include/pr.h): argument validation,
+// per-(device, stream) workspaces, launch-configuration lookup and tuning,
+// and the host-memory pipeline.  All arithmetic runs in the kernels.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pr.h"
+#include "kernels.cuh"
+#include "registry.h"
+
+namespace pr {
+
+// ------------------------------------------------------------------------
+// Kernel registry
+// ------------------------------------------------------------------------
+
+bool KernelKey::operator<(const KernelKey& o) const {
+    return std::tie(kind, dtype, op, prec, aux, unroll, vb) <
+           std::tie(o.kind, o.dtype, o.op, o.prec, o.aux, o.unroll, o.vb);
+}
+
+static std::map<KernelKey, KernelEntry>& table() {
+    static std::map<KernelKey, KernelEntry> t;
+    return t;
+}
+void reg_add(const KernelKey& k, const KernelEntry& e) { table()[k] = e; }
+const KernelEntry* reg_find(const KernelKey& k) {
+    auto it = table().find(k);
+    return it == table().end() ? nullptr : &it->second;
+}
+
+static void ensure_registered() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        register_f32();
+        register_f32_seg();
+        register_f16();
+        register_bf16();
+        register_f64();
+        register_i32();
+        register_u32();
+        register_i64();
+        register_backward();
+    });
+}
+
+// ------------------------------------------------------------------------
+// Errors
+// ------------------------------------------------------------------------
+
+static thread_local std::string g_msg;
+
+static pr_status fail(pr_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_msg = buf;
+    return s;
+}
+
+#define PR_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return fail(PR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------------
+// Types
+// ------------------------------------------------------------------------
+
+static bool valid_dtype(int d) { return d >= PR_F32 && d <= PR_I64; }
+static bool valid_op(int o) { return o >= PR_SUM && o <= PR_XOR; }
+static bool is_float(int d) { return d == PR_F32 || d == PR_F16 || d == PR_BF16 || d == PR_F64; }
+static int elem_size(int d) {
+    switch (d) {
+    case PR_F16: case PR_BF16: return 2;
+    case PR_F64: case PR_I64: return 8;
+    default: return 4;
+    }
+}
+static int out_size(int d, int op) { return elem_size((int)pr_out_dtype((pr_dtype)d, (pr_op)op)); }
+
+// ------------------------------------------------------------------------
+// Devices and workspaces
+// ------------------------------------------------------------------------
+
+struct DevInfo {
+    int sms = 0;
+    std::string name;
+};
+
+static std::mutex g_mu;
+static std::map<int, DevInfo> g_dev;
+struct WsRec {
+    Workspace ws;
+    void* base;
+    size_t bytes;
+};
+static std::map<std::pair<int, cudaStream_t>, WsRec> g_ws;
+
+static pr_status device_info(DevInfo* out, int* dev_out) {
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_dev.find(dev);
+    if (it == g_dev.end()) {
+        DevInfo d;
+        PR_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        cudaDeviceProp p;
+        PR_CUDA(cudaGetDeviceProperties(&p, dev));
+        d.name = p.name;
+        it = g_dev.emplace(dev, d).first;
+    }
+    *out = it->second;
+    if (dev_out) *dev_out = dev;
+    return PR_OK;
+}
+
+static size_t ws_bytes(int gmax) { return (size_t)3 * gmax * kSlot + (size_t)(gmax + 64) * 4; }
+
+static pr_status get_ws(cudaStream_t st, Workspace* out) {
+    DevInfo di;
+    int dev;
+    pr_status s = device_info(&di, &dev);
+    if (s != PR_OK) return s;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(dev, st);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) {
+        *out = it->second.ws;
+        return PR_OK;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    PR_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(PR_ERR_INVALID, "no workspace for this stream yet: call pr_prepare(stream) before graph capture");
+    const int gmax = di.sms * 32;
+    const size_t bytes = ws_bytes(gmax);
+    void* base = nullptr;
+    if (cudaMalloc(&base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PR_ERR_NOMEM, "workspace allocation of %zu bytes failed", bytes);
+    }
+    PR_CUDA(cudaMemsetAsync(base, 0, bytes, st));
+    Workspace ws;
+    char* b = static_cast<char*>(base);
+    ws.partials = b;
+    ws.head = b + (size_t)gmax * kSlot;
+    ws.tail = b + (size_t)2 * gmax * kSlot;
+    unsigned* u = reinterpret_cast<unsigned*>(b + (size_t)3 * gmax * kSlot);
+    ws.seg_cnt = u;
+    ws.counter = u + gmax;
+    ws.err = reinterpret_cast<int*>(u + gmax + 32);
+    ws.gmax = gmax;
+    g_ws[key] = WsRec{ws, base, bytes};
+    *out = ws;
+    return PR_OK;
+}
+
+// ------------------------------------------------------------------------
+// Launch configurations
+// ------------------------------------------------------------------------
+
+static int bucket_of(int64_t n) {
+    int b = 0;
+    while (b < 62 && ((int64_t)1 << (b + 1)) <= n) b++;
+    return n <= 0 ? 0 : b;
+}
+
+using CfgKey = std::tuple<int, int, int, int, int>;  // kind, dtype, op, precision, bucket
+static std::map<CfgKey, pr_config> g_tuned;
+
+// Built-in defaults (measured on GB300: two 32-byte loads in flight per thread
+// at 1024 resident threads per SM streams at the HBM limit for the plain
+// reduction); pr_autotune / pr_tune_load refine them per (dtype, op, size).
+static pr_config default_cfg(int kind, int dtype, int op, int prec) {
+    (void)dtype; (void)op; (void)prec;
+    if (kind == PR_KIND_BACKWARD) return pr_config{512, 4, 4, 16};
+    if (kind == PR_KIND_SEGMENTED) return pr_config{256, 4, 4, 32};
+    return pr_config{512, 2, 2, 32};
+}
+
+static bool cfg_valid(const pr_config& c) {
+    if (c.block < 64 || c.block > 1024 || c.block % 32) return false;
+    if (c.blocks_per_sm < 1 || c.blocks_per_sm > 32) return false;
+    if (c.unroll != 2 && c.unroll != 4) return false;
+    return c.vec_bytes == 16 || c.vec_bytes == 32;
+}
+
+static pr_config lookup_cfg(int kind, int dtype, int op, int prec, int64_t n) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_tuned.find(CfgKey{kind, dtype, op, prec, bucket_of(n)});
+    return it != g_tuned.end() ? it->second : default_cfg(kind, dtype, op, prec);
+}
+
+static std::map<std::pair<const void*, int>, int> g_occ;
+
+static pr_status occupancy(const void* fn, int block, int* bps) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(fn, block);
+    auto it = g_occ.find(key);
+    if (it == g_occ.end()) {
+        int nb = 0;
+        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0));
+        it = g_occ.emplace(key, nb).first;
+    }
+    *bps = it->second;
+    return PR_OK;
+}
+
+// Persistent grid: SMs x blocks-per-SM (clamped to what is resident at once).
+static pr_status persistent_grid(const KernelEntry* e, const pr_config& c, int sms, int gmax, int* grid) {
+    int occ = 0;
+    pr_status s = occupancy(e->fn, c.block, &occ);
+    if (s != PR_OK) return s;
+    if (occ < 1) return fail(PR_ERR_UNSUPPORTED, "kernel cannot run with %d threads per block", c.block);
+    const int bps = c.blocks_per_sm < occ ? c.blocks_per_sm : occ;
+    int g = sms * bps;
+    *grid = g < gmax ? g : gmax;
+    return PR_OK;
+}
+
+// ------------------------------------------------------------------------
+// Internal launches with an explicit configuration
+// ------------------------------------------------------------------------
+
+static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int prec, bool out_f64, void* out,
+                            void* part_out, cudaStream_t st, const pr_config& c) {
+    const KernelEntry* e = reg_find(KernelKey{K_REDUCE, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec, AUX_NONE,
+                                              (uint8_t)c.unroll, (uint8_t)c.vec_bytes});
+    if (!e) return fail(PR_ERR_UNSUPPORTED, "no reduce kernel for dtype %d op %d precision %d", dtype, op, prec);
+    DevInfo di;
+    pr_status s = device_info(&di, nullptr);
+    if (s != PR_OK) return s;
+    Workspace ws;
+    s = get_ws(st, &ws);
+    if (s != PR_OK) return s;
+    int grid = 0;
+    s = persistent_grid(e, c, di.sms, ws.gmax, &grid);
+    if (s != PR_OK) return s;
+    const int es = elem_size(dtype);
+    const int64_t ve = c.vec_bytes / es;
+    const int64_t per_block = (int64_t)c.block * ve * c.unroll;
+    const int64_t need = (n + per_block - 1) / per_block;
+    if (need < grid) grid = need < 1 ? 1 : (int)need;
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(x);
+    int64_t head = (int64_t)(((uintptr_t)c.vec_bytes - addr % (uintptr_t)c.vec_bytes) % (uintptr_t)c.vec_bytes) / es;
+    if (head > n) head = n;
+    ReduceArgs a{x, n, head, out, part_out, out_f64 ? 1 : 0, ws};
+    cudaError_t err = reinterpret_cast<ReduceLaunch>(e->launch)(a, grid, c.block, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "reduce launch: %s", cudaGetErrorString(err));
+    return PR_OK;
+}
+
+static pr_status run_segmented(const void* x, const int64_t* off, int64_t cols, int64_t nseg, int dtype, int op,
+                               int prec, int aux, void* out, int64_t* argidx, pr_prod_aux* paux, cudaStream_t st,
+                               const pr_config& c) {
+    const KernelEntry* e = reg_find(KernelKey{K_SEGMENTED, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec, (uint8_t)aux,
+                                              (uint8_t)c.unroll, (uint8_t)c.vec_bytes});
+    if (!e) return fail(PR_ERR_UNSUPPORTED, "no segmented kernel for dtype %d op %d precision %d aux %d", dtype, op,
+                        prec, aux);
+    DevInfo di;
+    pr_status s = device_info(&di, nullptr);
+    if (s != PR_OK) return s;
+    Workspace ws;
+    s = get_ws(st, &ws);
+    if (s != PR_OK) return s;
+    int grid = 0;
+    s = persistent_grid(e, c, di.sms, ws.gmax, &grid);
+    if (s != PR_OK) return s;
+    const int es = elem_size(dtype);
+    const int64_t shift = (int64_t)(reinterpret_cast<uintptr_t>(x) % (uintptr_t)c.vec_bytes) / es;
+    SegArgs a{x, off, cols, nseg, shift, out, argidx, paux, 0, ws};
+    cudaError_t err = reinterpret_cast<SegLaunch>(e->launch)(a, grid, c.block, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "segmented launch: %s", cudaGetErrorString(err));
+    return PR_OK;
+}
+
+static pr_status run_backward(int op, int dtype, const void* x, int64_t rows, int64_t cols, const void* g,
+                              const int64_t* argidx, const pr_prod_aux* aux, void* gi, cudaStream_t st,
+                              const pr_config& c) {
+    const KernelEntry* e = reg_find(KernelKey{K_BACKWARD, (uint8_t)dtype, 0, 0, 0, (uint8_t)c.unroll,
+                                              (uint8_t)c.vec_bytes});
+    if (!e) return fail(PR_ERR_UNSUPPORTED, "no backward kernel for dtype %d", dtype);
+    DevInfo di;
+    pr_status s = device_info(&di, nullptr);
+    if (s != PR_OK) return s;
+    int grid = 0;
+    s = persistent_grid(e, c, di.sms, 1 << 30, &grid);
+    if (s != PR_OK) return s;
+    const int es = elem_size(dtype);
+    const int64_t ve = c.vec_bytes / es;
+    const int64_t cv = (int64_t)c.block * c.unroll;
+    const int64_t nvec_max = cols / ve + 1;
+    const int64_t chunks = (nvec_max + cv - 1) / cv;
+    const int64_t tiles = rows * chunks;
+    if (tiles < grid) grid = (int)tiles;
+    const int64_t shift = (int64_t)(reinterpret_cast<uintptr_t>(gi) % (uintptr_t)c.vec_bytes) / es;
+    BwdArgs a{x, g, argidx, aux, gi, rows, cols, shift, chunks, op};
+    cudaError_t err = reinterpret_cast<BwdLaunch>(e->launch)(a, grid, c.block, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "backward launch: %s", cudaGetErrorString(err));
+    return PR_OK;
+}
+
+// ------------------------------------------------------------------------
+// Validation shared by the entry points
+// ------------------------------------------------------------------------
+
+static pr_status check_common(int dtype, int op, int prec) {
+    if (!valid_dtype(dtype)) return fail(PR_ERR_INVALID, "unknown dtype %d", dtype);
+    if (!valid_op(op)) return fail(PR_ERR_INVALID, "unknown op %d", op);
+    if (prec < PR_PREC_PLAIN || prec > PR_PREC_FP64_COMBINE) return fail(PR_ERR_INVALID, "unknown precision %d", prec);
+    if (is_float(dtype) && op >= PR_AND)
+        return fail(PR_ERR_UNSUPPORTED, "bitwise combiner %d is not defined on floating-point dtype %d", op, dtype);
+    if (prec != PR_PREC_PLAIN && !(op == PR_SUM && is_float(dtype) && dtype != PR_F64))
+        return fail(PR_ERR_UNSUPPORTED, "precision modes apply to fp32/fp16/bf16 SUM only");
+    return PR_OK;
+}
+
+static pr_status check_aligned(const void* p, int dtype, const char* what) {
+    if (p && reinterpret_cast<uintptr_t>(p) % (uintptr_t)elem_size(dtype))
+        return fail(PR_ERR_INVALID, "%s is not aligned to its element size", what);
+    return PR_OK;
+}
+
+}  // namespace pr
+
+using namespace pr;
+
+// ------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------
+
+extern "C" {
+
+pr_dtype pr_out_dtype(pr_dtype dtype, pr_op op) {
+    if (dtype == PR_F16 || dtype == PR_BF16) return (op == PR_MAX || op == PR_MIN) ? dtype : PR_F32;
+    if (dtype == PR_I32 && op == PR_SUM) return PR_I64;
+    return dtype;
+}
+
+const char* pr_status_string(pr_status s) {
+    switch (s) {
+    case PR_OK: return "PR_OK";
+    case PR_ERR_INVALID: return "PR_ERR_INVALID";
+    case PR_ERR_UNSUPPORTED: return "PR_ERR_UNSUPPORTED";
+    case PR_ERR_CUDA: return "PR_ERR_CUDA";
+    case PR_ERR_TIMEOUT: return "PR_ERR_TIMEOUT";
+    case PR_ERR_NOMEM: return "PR_ERR_NOMEM";
+    default: return "PR_ERR_UNKNOWN";
+    }
+}
+
+const char* pr_last_error_message(void) { return g_msg.c_str(); }
+
+const char* pr_version(void) { return "pr 0.1 (sm_103a)"; }
+
+pr_status pr_reduce_ex(const void* x, int64_t n, pr_dtype dtype, pr_op op, pr_precision precision,
+                       pr_dtype out_dtype, void* out, pr_stream_t stream) {
+    g_msg.clear();
+    pr_status s = check_common(dtype, op, precision);
+    if (s != PR_OK) return s;
+    if (n < 0) return fail(PR_ERR_INVALID, "n must be >= 0 (got %lld)", (long long)n);
+    if (!x && n > 0) return fail(PR_ERR_INVALID, "x is NULL");
+    if (!out) return fail(PR_ERR_INVALID, "out is NULL");
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    const pr_dtype def = pr_out_dtype(dtype, op);
+    const bool f64 = out_dtype != def;
+    if (f64 && !(out_dtype == PR_F64 && precision != PR_PREC_PLAIN))
+        return fail(PR_ERR_UNSUPPORTED, "out_dtype %d not available for dtype %d op %d", out_dtype, dtype, op);
+    ensure_registered();
+    const pr_config c = lookup_cfg(PR_KIND_REDUCE, dtype, op, precision, n);
+    return run_reduce(x, n, dtype, op, precision, f64, out, nullptr, (cudaStream_t)stream, c);
+}
+
+pr_status pr_reduce(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* out, pr_stream_t stream) {
+    if (!valid_dtype(dtype) || !valid_op(op)) {
+        g_msg.clear();
+        return check_common(dtype, op, PR_PREC_PLAIN);
+    }
+    return pr_reduce_ex(x, n, dtype, op, PR_PREC_PLAIN, pr_out_dtype(dtype, op), out, stream);
+}
+
+static pr_status segmented_common(const void* x, const int64_t* offsets, int64_t cols, int64_t nseg, pr_dtype dtype,
+                                  pr_op op, pr_precision precision, void* out, int64_t* argidx, pr_prod_aux* aux,
+                                  pr_stream_t stream) {
+    pr_status s = check_common(dtype, op, precision);
+    if (s != PR_OK) return s;
+    if (nseg < 0) return fail(PR_ERR_INVALID, "number of segments must be >= 0");
+    if (nseg == 0) return PR_OK;
+    if (!out) return fail(PR_ERR_INVALID, "out is NULL");
+    if (argidx && op != PR_MAX && op != PR_MIN) return fail(PR_ERR_UNSUPPORTED, "argidx needs MAX or MIN");
+    if (aux && !(op == PR_PROD && (dtype == PR_F32 || dtype == PR_F64)))
+        return fail(PR_ERR_UNSUPPORTED, "product aux needs PROD on F32 or F64");
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    const int auxk = argidx ? AUX_ARG : (aux ? AUX_PROD : AUX_NONE);
+    ensure_registered();
+    const pr_config c = lookup_cfg(PR_KIND_SEGMENTED, dtype, op, precision, nseg);
+    return run_segmented(x, offsets, cols, nseg, dtype, op, precision, auxk, out, argidx, aux, (cudaStream_t)stream, c);
+}
+
+pr_status pr_segmented_reduce_aux(const void* x, const int64_t* offsets, int64_t nseg, pr_dtype dtype, pr_op op,
+                                  pr_precision precision, void* out, int64_t* argidx, pr_prod_aux* aux,
+                                  pr_stream_t stream) {
+    g_msg.clear();
+    if (nseg > 0 && !offsets) return fail(PR_ERR_INVALID, "offsets is NULL");
+    if (nseg > 0 && !x) return fail(PR_ERR_INVALID, "x is NULL");
+    return segmented_common(x, offsets, 0, nseg, dtype, op, precision, out, argidx, aux, stream);
+}
+
+pr_status pr_segmented_reduce(const void* x, const int64_t* offsets, int64_t nseg, pr_dtype dtype, pr_op op,
+                              void* out, pr_stream_t stream) {
+    return pr_segmented_reduce_aux(x, offsets, nseg, dtype, op, PR_PREC_PLAIN, out, nullptr, nullptr, stream);
+}
+
+pr_status pr_reduce_rows(const void* x, int64_t rows, int64_t cols, pr_dtype dtype, pr_op op, pr_precision precision,
+                         void* out, int64_t* argidx, pr_prod_aux* aux, pr_stream_t stream) {
+    g_msg.clear();
+    if (rows < 0 || cols < 0) return fail(PR_ERR_INVALID, "rows and cols must be >= 0");
+    if (cols > 0 && rows > ((int64_t)1 << 62) / cols) return fail(PR_ERR_INVALID, "rows*cols overflows");
+    if (rows > 0 && cols > 0 && !x) return fail(PR_ERR_INVALID, "x is NULL");
+    return segmented_common(x, nullptr, cols, rows, dtype, op, precision, out, argidx, aux, stream);
+}
+
+pr_status pr_reduce_backward(pr_op op, pr_dtype dtype, const void* x, int64_t rows, int64_t cols,
+                             const void* grad_out, const int64_t* argidx, const pr_prod_aux* aux, void* grad_in,
+                             pr_stream_t stream) {
+    g_msg.clear();
+    if (dtype != PR_F32 && dtype != PR_F64) return fail(PR_ERR_UNSUPPORTED, "backward supports F32 and F64");
+    if (op != PR_SUM && op != PR_MAX && op != PR_MIN && op != PR_PROD)
+        return fail(PR_ERR_UNSUPPORTED, "backward supports SUM, MAX, MIN and PROD");
+    if (rows < 0 || cols < 0) return fail(PR_ERR_INVALID, "rows and cols must be >= 0");
+    if (cols > 0 && rows > ((int64_t)1 << 62) / cols) return fail(PR_ERR_INVALID, "rows*cols overflows");
+    if (rows == 0 || cols == 0) return PR_OK;
+    if (!grad_out || !grad_in) return fail(PR_ERR_INVALID, "grad_out / grad_in is NULL");
+    if ((op == PR_MAX || op == PR_MIN) && !argidx) return fail(PR_ERR_INVALID, "MAX/MIN backward needs argidx");
+    if (op == PR_PROD && (!aux || !x)) return fail(PR_ERR_INVALID, "PROD backward needs x and aux");
+    pr_status s;
+    if ((s = check_aligned(grad_in, dtype, "grad_in")) != PR_OK) return s;
+    if ((s = check_aligned(grad_out, dtype, "grad_out")) != PR_OK) return s;
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    ensure_registered();
+    const pr_config c = lookup_cfg(PR_KIND_BACKWARD, dtype, op, 0, rows * cols);
+    return run_backward(op, dtype, x, rows, cols, grad_out, argidx, aux, grad_in, (cudaStream_t)stream, c);
+}
+
+pr_status pr_prepare(pr_stream_t stream) {
+    g_msg.clear();
+    ensure_registered();
+    Workspace ws;
+    return get_ws((cudaStream_t)stream, &ws);
+}
+
+pr_status pr_last_device_error(pr_stream_t stream, int32_t* code) {
+    g_msg.clear();
+    if (!code) return fail(PR_ERR_INVALID, "code is NULL");
+    *code = PR_OK;
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    Workspace ws;
+    bool have = false;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_ws.find(std::make_pair(dev, (cudaStream_t)stream));
+        if (it != g_ws.end()) { ws = it->second.ws; have = true; }
+    }
+    PR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (!have) return PR_OK;
+    int32_t v = 0;
+    PR_CUDA(cudaMemcpy(&v, ws.err, sizeof v, cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        // A launch that saw malformed input may have left tickets armed: re-zero them.
+        PR_CUDA(cudaMemset(ws.seg_cnt, 0, (size_t)(ws.gmax + 64) * 4));
+        *code = v;
+    }
+    return PR_OK;
+}
+
+// ------------------------------------------------------------------------
+// End to end from host memory
+// ------------------------------------------------------------------------
+
+namespace {
+struct HostPipe {
+    char* stage[2] = {nullptr, nullptr};
+    char* parts = nullptr;
+    size_t parts_cap = 0;
+    void* dout = nullptr;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    cudaEvent_t consumed[2] = {nullptr, nullptr};
+};
+std::map<int, HostPipe> g_pipes;
+std::mutex g_pipe_mu;
+constexpr size_t kChunkBytes = (size_t)64 << 20;
+}  // namespace
+
+pr_status pr_reduce_host(const void* host_x, int64_t n, pr_dtype dtype, pr_op op, void* host_out,
+                         pr_stream_t stream) {
+    g_msg.clear();
+    pr_status s = check_common(dtype, op, PR_PREC_PLAIN);
+    if (s != PR_OK) return s;
+    if (n < 0) return fail(PR_ERR_INVALID, "n must be >= 0");
+    if (!host_x && n > 0) return fail(PR_ERR_INVALID, "host_x is NULL");
+    if (!host_out) return fail(PR_ERR_INVALID, "host_out is NULL");
+    if ((s = check_aligned(host_x, dtype, "host_x")) != PR_OK) return s;
+    ensure_registered();
+    const KernelEntry* ce = reg_find(KernelKey{K_COMBINE, (uint8_t)dtype, (uint8_t)op, 0, AUX_NONE, 0, 0});
+    if (!ce) return fail(PR_ERR_UNSUPPORTED, "no combine kernel for dtype %d op %d", dtype, op);
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    HostPipe& hp = g_pipes[dev];
+    if (!hp.stage[0]) {
+        for (int b = 0; b < 2; b++) {
+            PR_CUDA(cudaMalloc(&hp.stage[b], kChunkBytes));
+            PR_CUDA(cudaEventCreateWithFlags(&hp.copied[b], cudaEventDisableTiming));
+            PR_CUDA(cudaEventCreateWithFlags(&hp.consumed[b], cudaEventDisableTiming));
+        }
+        PR_CUDA(cudaMalloc(&hp.dout, 64));
+        PR_CUDA(cudaStreamCreateWithFlags(&hp.copy, cudaStreamNonBlocking));
+    }
+    const int es = elem_size(dtype);
+    const int64_t chunk = (int64_t)(kChunkBytes / (size_t)es);
+    const int64_t nchunks = n == 0 ? 1 : (n + chunk - 1) / chunk;
+    if ((size_t)nchunks * kSlot > hp.parts_cap) {
+        if (hp.parts) PR_CUDA(cudaFree(hp.parts));
+        hp.parts_cap = (size_t)nchunks * kSlot;
+        PR_CUDA(cudaMalloc(&hp.parts, hp.parts_cap));
+    }
+    const pr_config c = lookup_cfg(PR_KIND_REDUCE, dtype, op, 0, chunk < n ? chunk : n);
+    // the copy stream starts after everything already queued on `st`
+    PR_CUDA(cudaEventRecord(hp.consumed[0], st));
+    PR_CUDA(cudaStreamWaitEvent(hp.copy, hp.consumed[0], 0));
+    PR_CUDA(cudaEventRecord(hp.consumed[1], st));
+    for (int64_t k = 0; k < nchunks; k++) {
+        const int b = (int)(k & 1);
+        const int64_t lo = k * chunk;
+        const int64_t len = n - lo < chunk ? n - lo : chunk;
+        PR_CUDA(cudaStreamWaitEvent(hp.copy, hp.consumed[b], 0));
+        if (len > 0)
+            PR_CUDA(cudaMemcpyAsync(hp.stage[b], static_cast<const char*>(host_x) + lo * es, (size_t)len * es,
+                                    cudaMemcpyHostToDevice, hp.copy));
+        PR_CUDA(cudaEventRecord(hp.copied[b], hp.copy));
+        PR_CUDA(cudaStreamWaitEvent(st, hp.copied[b], 0));
+        s = run_reduce(hp.stage[b], len, dtype, op, 0, false, nullptr, hp.parts + k * kSlot, st, c);
+        if (s != PR_OK) return s;
+        PR_CUDA(cudaEventRecord(hp.consumed[b], st));
+    }
+    cudaError_t err = reinterpret_cast<CombineLaunch>(ce->launch)(hp.parts, (int)nchunks, hp.dout, 0, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "combine launch: %s", cudaGetErrorString(err));
+    PR_CUDA(cudaMemcpyAsync(host_out, hp.dout, (size_t)out_size(dtype, op), cudaMemcpyDeviceToHost, st));
+    PR_CUDA(cudaStreamSynchronize(st));
+    return PR_OK;
+}
+
+// ------------------------------------------------------------------------
+// Tuning
+// ------------------------------------------------------------------------
+
+pr_status pr_get_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision precision, int64_t n, pr_config* cfg) {
+    g_msg.clear();
+    if (!cfg) return fail(PR_ERR_INVALID, "cfg is NULL");
+    if (kind < PR_KIND_REDUCE || kind > PR_KIND_BACKWARD) return fail(PR_ERR_INVALID, "unknown kind");
+    *cfg = lookup_cfg(kind, dtype, op, precision, n);
+    return PR_OK;
+}
+
+pr_status pr_set_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision precision, int64_t n,
+                        const pr_config* cfg) {
+    g_msg.clear();
+    if (!cfg || !cfg_valid(*cfg)) return fail(PR_ERR_INVALID, "invalid configuration");
+    if (kind < PR_KIND_REDUCE || kind > PR_KIND_BACKWARD) return fail(PR_ERR_INVALID, "unknown kind");
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tuned[CfgKey{kind, dtype, op, precision, bucket_of(n)}] = *cfg;
+    return PR_OK;
+}
+
+pr_status pr_autotune(pr_kind kind, const void* x, int64_t n, const int64_t* offsets, int64_t nseg, pr_dtype dtype,
+                      pr_op op, pr_precision precision, pr_stream_t stream, pr_config* best) {
+    g_msg.clear();
+    pr_status s = check_common(dtype, op, precision);
+    if (s != PR_OK) return s;
+    if (kind != PR_KIND_REDUCE && kind != PR_KIND_SEGMENTED)
+        return fail(PR_ERR_UNSUPPORTED, "autotune covers PR_KIND_REDUCE and PR_KIND_SEGMENTED");
+    if (kind == PR_KIND_REDUCE && (n <= 0 || !x)) return fail(PR_ERR_INVALID, "autotune needs data (x, n > 0)");
+    if (kind == PR_KIND_SEGMENTED && (nseg <= 0 || !offsets || !x))
+        return fail(PR_ERR_INVALID, "autotune needs x, offsets and nseg > 0");
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    ensure_registered();
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    PR_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return fail(PR_ERR_INVALID, "autotune cannot run during capture");
+    const int64_t nout = kind == PR_KIND_SEGMENTED ? nseg : 1;
+    void* dout = nullptr;
+    PR_CUDA(cudaMalloc(&dout, (size_t)nout * 8));
+    cudaEvent_t e0, e1;
+    PR_CUDA(cudaEventCreate(&e0));
+    PR_CUDA(cudaEventCreate(&e1));
+    const bool f64 = false;
+    float best_ms = 1e30f;
+    pr_config best_c = default_cfg(kind, dtype, op, precision);
+    const int blocks[] = {256, 512, 1024};
+    const int bpss[] = {1, 2, 4, 8};
+    for (int blk : blocks)
+        for (int bps : bpss) {
+            if (blk * bps > 2048) continue;
+            for (int u : kUnrolls)
+                for (int vb : kVecBytes) {
+                    const pr_config c{blk, bps, u, vb};
+                    auto run = [&]() -> pr_status {
+                        if (kind == PR_KIND_REDUCE)
+                            return run_reduce(x, n, dtype, op, precision, f64, dout, nullptr, st, c);
+                        return run_segmented(x, offsets, 0, nseg, dtype, op, precision, AUX_NONE, dout, nullptr,
+                                             nullptr, st, c);
+                    };
+                    bool ok = true;
+                    for (int w = 0; w < 2 && ok; w++) ok = run() == PR_OK;
+                    if (!ok) continue;
+                    float t_min = 1e30f;
+                    for (int r = 0; r < 5 && ok; r++) {
+                        PR_CUDA(cudaEventRecord(e0, st));
+                        ok = run() == PR_OK;
+                        PR_CUDA(cudaEventRecord(e1, st));
+                        PR_CUDA(cudaEventSynchronize(e1));
+                        float ms = 0;
+                        PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                        t_min = ms < t_min ? ms : t_min;
+                    }
+                    if (ok && t_min < best_ms) {
+                        best_ms = t_min;
+                        best_c = c;
+                    }
+                }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dout);
+    g_msg.clear();
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_tuned[CfgKey{kind, dtype, op, precision, bucket_of(kind == PR_KIND_SEGMENTED ? nseg : n)}] = best_c;
+    }
+    if (best) *best = best_c;
+    return PR_OK;
+}
+
+pr_status pr_tune_save(const char* path) {
+    g_msg.clear();
+    if (!path) return fail(PR_ERR_INVALID, "path is NULL");
+    DevInfo di;
+    pr_status s = device_info(&di, nullptr);
+    if (s != PR_OK) return s;
+    FILE* f = fopen(path, "w");
+    if (!f) return fail(PR_ERR_INVALID, "cannot open %s for writing", path);
+    std::lock_guard<std::mutex> lk(g_mu);
+    fprintf(f, "{\"gpu\": \"%s\", \"entries\": [\n", di.name.c_str());
+    bool first = true;
+    for (auto& kv : g_tuned) {
+        int kind, dtype, op, prec, bucket;
+        std::tie(kind, dtype, op, prec, bucket) = kv.first;
+        const pr_config& c = kv.second;
+        fprintf(f, "%s {\"kind\": %d, \"dtype\": %d, \"op\": %d, \"precision\": %d, \"bucket\": %d, \"block\": %d, "
+                   "\"blocks_per_sm\": %d, \"unroll\": %d, \"vec_bytes\": %d}",
+                first ? "" : ",\n", kind, dtype, op, prec, bucket, c.block, c.blocks_per_sm, c.unroll, c.vec_bytes);
+        first = false;
+    }
+    fprintf(f, "\n]}\n");
+    fclose(f);
+    return PR_OK;
+}
+
+pr_status pr_tune_load(const char* path) {
+    g_msg.clear();
+    if (!path) return fail(PR_ERR_INVALID, "path is NULL");
+    DevInfo di;
+    pr_status s = device_info(&di, nullptr);
+    if (s != PR_OK) return s;
+    FILE* f = fopen(path, "r");
+    if (!f) return fail(PR_ERR_INVALID, "cannot open %s", path);
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
+    fclose(f);
+    const std::string want = "\"gpu\": \"" + di.name + "\"";
+    if (text.find(want) == std::string::npos) return fail(PR_ERR_INVALID, "tuning file is for another GPU");
+    size_t pos = 0;
+    int loaded = 0;
+    std::map<CfgKey, pr_config> fresh;
+    while ((pos = text.find("{\"kind\"", pos)) != std::string::npos) {
+        int kind, dtype, op, prec, bucket;
+        pr_config c;
+        if (sscanf(text.c_str() + pos,
+                   "{\"kind\": %d, \"dtype\": %d, \"op\": %d, \"precision\": %d, \"bucket\": %d, \"block\": %d, "
+                   "\"blocks_per_sm\": %d, \"unroll\": %d, \"vec_bytes\": %d}",
+                   &kind, &dtype, &op, &prec, &bucket, &c.block, &c.blocks_per_sm, &c.unroll, &c.vec_bytes) != 9 ||
+            !cfg_valid(c))
+            return fail(PR_ERR_INVALID, "malformed tuning entry at byte %zu", pos);
+        fresh[CfgKey{kind, dtype, op, prec, bucket}] = c;
+        loaded++;
+        pos++;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& kv : fresh) g_tuned[kv.first] = kv.second;
+    return PR_OK;
+}
+
+}  // extern "C"

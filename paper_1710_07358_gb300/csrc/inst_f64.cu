@@ -1,0 +1,15 @@
+// fp64 kernels.  The product runs on the integer pipes (ProdExt); the sum uses
+// fp64 adds; max/min compare integer keys.
+#include "launch.cuh"
+
+namespace pr {
+void register_f64() {
+    reg_family<SumF64>(PR_F64, PR_SUM, PR_PREC_PLAIN, AUX_NONE, true, true);
+    reg_family<ProdExt>(PR_F64, PR_PROD, PR_PREC_PLAIN, AUX_NONE, true, true);
+    reg_family<MaxMin<KeyF64, true>>(PR_F64, PR_MAX, PR_PREC_PLAIN, AUX_NONE, true, true);
+    reg_family<MaxMin<KeyF64, false>>(PR_F64, PR_MIN, PR_PREC_PLAIN, AUX_NONE, true, true);
+    reg_family<ArgExt<KeyF64, true>>(PR_F64, PR_MAX, PR_PREC_PLAIN, AUX_ARG, false, true);
+    reg_family<ArgExt<KeyF64, false>>(PR_F64, PR_MIN, PR_PREC_PLAIN, AUX_ARG, false, true);
+    reg_family<ProdAux<ProdExt>>(PR_F64, PR_PROD, PR_PREC_PLAIN, AUX_PROD, false, true);
+}
+}  // namespace pr

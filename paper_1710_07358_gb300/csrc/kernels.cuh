@@ -1,0 +1,400 @@
+// Reduction kernels.  Included by the per-dtype instantiation units only.
+//
+// k_reduce     plain reduction of x[0..n) in ONE launch:
+//   Step 1 (Section 2.3 / Section 3, "Unrolling the step 1"): a persistent grid
+//     (Section 2.5) strides over the input in VB-byte vectors; each thread keeps
+//     U independent accumulators and issues its U loads before accumulating,
+//     so U*VB bytes per thread are in flight.  Elements before the first VB
+//     boundary and after the last full vector are read as scalars (no access
+//     outside [x, x+n); the identity is never needed as a load mask).
+//   Step 3: the U accumulators are combined, then the warp (shuffle butterfly
+//     or redux.sync), then the block (one value per warp in shared memory).
+//   Stage 2 (Section 2.3), fused: every block stores its partial; the last
+//     block to finish (atomic ticket after a fence) combines all partials in
+//     block-index order, writes the result and re-arms the ticket counter.
+//
+// k_segmented  many reductions (segments of a CSR offsets array, or equal rows)
+//   in one launch.  The element range [offsets[0], offsets[nseg]) is cut into
+//   tiles of blockDim*U*VB bytes and every block owns a contiguous run of
+//   tiles.  Inside a tile that lies in one segment the block streams exactly
+//   like k_reduce; a tile containing segment boundaries emits the finished
+//   segment, reduces the segments that lie wholly inside the tile (short ones
+//   one per warp, long ones with the whole block) and starts the next one.
+//   A segment that crosses block boundaries leaves one partial per block it
+//   touches (its first block's "tail" slot, later blocks' "head" slots); the
+//   last of those blocks to arrive (per-segment ticket) combines them in block
+//   order.  Results are deterministic for a fixed launch configuration.
+//
+// k_combine_parts  one block combining an array of partials in order.
+#pragma once
+#include "traits.cuh"
+
+namespace pr {
+
+constexpr int kSlot = 64;      // bytes per partial slot (>= sizeof(Part) of every trait)
+constexpr int kSmallSeg = 512; // segments up to this length are reduced by one warp
+enum : int { kErrInvalid = 1, kErrTimeout = 4 };
+
+struct Workspace {
+    char* partials;      // gmax slots (k_reduce)
+    char* head;          // gmax slots (k_segmented: first-segment partial of a block)
+    char* tail;          // gmax slots (k_segmented: last-segment partial of a block)
+    unsigned* seg_cnt;   // gmax tickets (k_segmented), zero between launches
+    unsigned* counter;   // 1 ticket (k_reduce), zero between launches
+    int* err;            // device error word
+    int gmax;
+};
+
+struct ReduceArgs {
+    const void* x;
+    int64_t n;
+    int64_t head;        // elements before the first VB-aligned element (< VE, <= n)
+    void* out;
+    void* part_out;      // non-null: store the final Part here instead of a result
+    int out_f64;
+    Workspace ws;
+};
+
+struct SegArgs {
+    const void* x;
+    const int64_t* off;  // nseg+1 CSR offsets, or null for equal rows of `cols`
+    int64_t cols;
+    int64_t nseg;
+    int64_t shift;       // x's element offset from the previous VB boundary
+    void* out;
+    int64_t* argidx;
+    pr_prod_aux* aux;
+    int out_f64;
+    Workspace ws;
+};
+
+struct BwdArgs {
+    const void* x;
+    const void* g;
+    const int64_t* argidx;
+    const pr_prod_aux* aux;
+    void* gi;
+    int64_t rows, cols;
+    int64_t shift;           // grad_in's element offset from the previous VB boundary
+    int64_t chunks_per_row;
+    int op;
+};
+
+
+template <class T>
+__device__ __forceinline__ typename T::Part* slot(char* base, int64_t i) {
+    return reinterpret_cast<typename T::Part*>(base + i * kSlot);
+}
+
+template <class T, int U>
+__device__ __forceinline__ typename T::Part fold(typename T::Acc (&acc)[U]) {
+    typename T::Part p = T::to_part(acc[0]);
+#pragma unroll
+    for (int u = 1; u < U; u++) p = T::combine(p, T::to_part(acc[u]));
+    return p;
+}
+
+// ------------------------------------------------------------------------
+// Plain reduction
+// ------------------------------------------------------------------------
+
+template <class T, int U, int VB>
+__global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a) {
+    using Ld = typename T::Ld;
+    using In = typename Ld::In;
+    using E = typename Ld::E;
+    using Part = typename T::Part;
+    constexpr int VE = VB / Ld::ES;
+    const In* x = static_cast<const In*>(a.x);
+
+    typename T::Acc acc[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) acc[u] = T::init();
+
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t head = a.head;
+    const int64_t nvec = (a.n - head) / VE;
+    const char* xv = reinterpret_cast<const char*>(x + head);
+
+    int64_t i = tid;
+    for (; i + (int64_t)(U - 1) * nth < nvec; i += (int64_t)U * nth) {
+        Words<VB> w[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) w[u] = ldv<VB>(xv + (i + u * nth) * VB);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            E e[VE];
+            Ld::template dec<VB>(w[u], e);
+            T::add_vec(acc[u], e, head + (i + u * nth) * VE);
+        }
+    }
+    for (; i < nvec; i += nth) {
+        Words<VB> w = ldv<VB>(xv + i * VB);
+        E e[VE];
+        Ld::template dec<VB>(w, e);
+        T::add_vec(acc[0], e, head + i * VE);
+    }
+    if (tid < head) T::add(acc[0], Ld::one(x, tid), tid);
+    for (int64_t j = head + nvec * VE + tid; j < a.n; j += nth) T::add(acc[0], Ld::one(x, j), j);
+
+    Part p = block_combine<T>(fold<T, U>(acc));
+
+    __shared__ unsigned s_last;
+    if (threadIdx.x == 0) {
+        *slot<T>(a.ws.partials, blockIdx.x) = p;
+        __threadfence();
+        const unsigned ticket = atomicAdd(a.ws.counter, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    Part q = T::part_init();
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) q = T::combine(q, ld_cg_any(slot<T>(a.ws.partials, j)));
+    q = block_combine<T>(q);
+    if (threadIdx.x == 0) {
+        if (a.part_out) *static_cast<Part*>(a.part_out) = q;
+        else T::store(a.out, 0, q, a.out_f64 != 0);
+        *a.ws.counter = 0u;
+    }
+}
+
+// One block: out = parts[0] (x) parts[1] (x) ... in index order (slot stride kSlot).
+template <class T>
+__global__ void __launch_bounds__(256) k_combine_parts(const char* parts, int count, void* out, int out_f64) {
+    using Part = typename T::Part;
+    Part q = T::part_init();
+    for (int j = threadIdx.x; j < count; j += blockDim.x)
+        q = T::combine(q, *reinterpret_cast<const Part*>(parts + (int64_t)j * kSlot));
+    q = block_combine<T>(q);
+    if (threadIdx.x == 0) T::store(out, 0, q, out_f64 != 0);
+}
+
+// ------------------------------------------------------------------------
+// Segmented reduction
+// ------------------------------------------------------------------------
+
+struct Segs {
+    const int64_t* off;
+    int64_t cols, nseg, P0, P1;
+    __device__ __forceinline__ int64_t raw(int64_t s) const { return off ? __ldg(off + s) : s * cols; }
+    // segment bounds clamped to [P0, P1]: malformed offsets cannot move a read
+    // outside the range the caller vouches for
+    __device__ __forceinline__ int64_t begin(int64_t s) const {
+        const int64_t b = raw(s);
+        return b < P0 ? P0 : (b > P1 ? P1 : b);
+    }
+    __device__ __forceinline__ int64_t end(int64_t s) const { return begin(s + 1); }
+    // largest s in [lo, nseg) with begin(s) <= p   (requires begin(lo) <= p)
+    __device__ int64_t find(int64_t lo, int64_t p) const {
+        if (!off) {
+            int64_t s = p / cols;
+            s = s < lo ? lo : s;
+            return s > nseg - 1 ? nseg - 1 : s;
+        }
+        int64_t l = lo, r = nseg - 1;
+        while (l < r) {
+            const int64_t m = (l + r + 1) >> 1;
+            if (begin(m) <= p) l = m; else r = m - 1;
+        }
+        return l;
+    }
+};
+
+template <class T, int U, int VB>
+struct SegCtx {
+    using Ld = typename T::Ld;
+    using In = typename Ld::In;
+    using E = typename Ld::E;
+    static constexpr int VE = VB / Ld::ES;
+    const In* x;
+    Segs sg;
+    int64_t P0, P1;
+
+    // Accumulate the elements with position in [lo, hi) among the U vectors
+    // this thread owns in the tile starting at position tlo.
+    __device__ __forceinline__ void masked(typename T::Acc (&acc)[U], int64_t tlo, int64_t lo, int64_t hi) const {
+        if (lo >= hi) return;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t vp = tlo + ((int64_t)u * blockDim.x + threadIdx.x) * VE;
+            if (vp + VE <= lo || vp >= hi) continue;
+            if (vp >= P0 && vp + VE <= P1) {
+                const Words<VB> w = ldv<VB>(x + vp);
+                E e[VE];
+                Ld::template dec<VB>(w, e);
+#pragma unroll
+                for (int k = 0; k < VE; k++)
+                    if (vp + k >= lo && vp + k < hi) T::add(acc[u], e[k], vp + k);
+            } else {
+                const int64_t a0 = vp > lo ? vp : lo;
+                const int64_t a1 = vp + VE < hi ? vp + VE : hi;
+                for (int64_t p = a0; p < a1; p++) T::add(acc[u], Ld::one(x, p), p);
+            }
+        }
+    }
+};
+
+template <class T, int U, int VB>
+__global__ void __launch_bounds__(1024) k_segmented(SegArgs a) {
+    using Ld = typename T::Ld;
+    using In = typename Ld::In;
+    using E = typename Ld::E;
+    using Acc = typename T::Acc;
+    using Part = typename T::Part;
+    constexpr int VE = VB / Ld::ES;
+    const In* x = static_cast<const In*>(a.x);
+    const int64_t nseg = a.nseg;
+    const bool f64 = a.out_f64 != 0;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    if (nseg <= 0) return;
+
+    Segs sg{a.off, a.cols, nseg, 0, 0};
+    const int64_t raw0 = sg.raw(0), rawN = sg.raw(nseg);
+    const int64_t P0 = raw0 < 0 ? 0 : raw0;
+    const int64_t P1 = rawN < P0 ? P0 : rawN;
+    sg.P0 = P0;
+    sg.P1 = P1;
+
+    // Empty segments get the identity; malformed offsets raise the error word.
+    for (int64_t s = gtid; s < nseg; s += nth) {
+        const int64_t rb = sg.raw(s), re = sg.raw(s + 1);
+        if (rb > re || rb < 0) atomicOr(a.ws.err, kErrInvalid);
+        if (sg.begin(s) == sg.end(s)) T::store_empty(a.out, s, f64, a.argidx, a.aux);
+    }
+    if (P1 <= P0) return;
+
+    const int B = blockDim.x;
+    const int64_t TILE = (int64_t)B * VE * U;
+    const int64_t shift = a.shift;
+    const int64_t J0 = ((P0 + shift) / VE) * VE;  // first VB boundary at or before P0
+    const int64_t ntiles = (P1 + shift - J0 + TILE - 1) / TILE;
+    const int64_t K = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * K;
+    const int64_t t1 = t0 + K < ntiles ? t0 + K : ntiles;
+    if (t0 >= t1) return;
+    const int64_t CB = K * TILE;
+    const int64_t blk_lo = (J0 + t0 * TILE - shift) > P0 ? (J0 + t0 * TILE - shift) : P0;
+    const int64_t blk_hi = (J0 + t1 * TILE - shift) < P1 ? (J0 + t1 * TILE - shift) : P1;
+
+    SegCtx<T, U, VB> ctx{x, sg, P0, P1};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = B >> 5;
+
+    __shared__ int64_t s_i64;
+    __shared__ int s_fin;
+
+    // Finish this block's piece of segment s (all threads call).
+    auto emit = [&](int64_t s, Acc (&acc)[U]) {
+        Part p = block_combine<T>(fold<T, U>(acc));
+#pragma unroll
+        for (int u = 0; u < U; u++) acc[u] = T::init();
+        const int64_t sb = sg.begin(s), se = sg.end(s);
+        if (sb >= blk_lo && se <= blk_hi) {
+            if (threadIdx.x == 0) {
+                T::store(a.out, s, p, f64);
+                T::store_aux(a.argidx, a.aux, s, p, sb);
+            }
+            return;
+        }
+        const int64_t ba = (sb + shift - J0) / CB, bb = (se - 1 + shift - J0) / CB;
+        if (threadIdx.x == 0) {
+            *slot<T>(sb < blk_lo ? a.ws.head : a.ws.tail, blockIdx.x) = p;
+            __threadfence();
+            const unsigned old = atomicAdd(a.ws.seg_cnt + ba, 1u);
+            s_fin = (old == (unsigned)(bb - ba));
+        }
+        __syncthreads();
+        if (s_fin && warp == 0) {
+            __threadfence();
+            Part q = T::part_init();
+            for (int64_t k = lane; k <= bb - ba; k += 32)
+                q = T::combine(q, ld_cg_any(k == 0 ? slot<T>(a.ws.tail, ba) : slot<T>(a.ws.head, ba + k)));
+            q = T::warp_reduce(q);
+            if (lane == 0) {
+                T::store(a.out, s, q, f64);
+                T::store_aux(a.argidx, a.aux, s, q, sb);
+                a.ws.seg_cnt[ba] = 0u;
+            }
+        }
+        __syncthreads();
+    };
+
+    if (threadIdx.x == 0) s_i64 = sg.find(0, blk_lo);
+    __syncthreads();
+    int64_t cs = s_i64;
+
+    Acc acc[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) acc[u] = T::init();
+
+    for (int64_t t = t0; t < t1; t++) {
+        const int64_t tlo = J0 + t * TILE - shift, thi = tlo + TILE;
+        const int64_t cend = sg.end(cs);
+        if (cend >= thi && tlo >= P0 && thi <= P1) {
+            // the whole tile lies inside segment cs: stream it
+            Words<VB> w[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) w[u] = ldv<VB>(x + tlo + ((int64_t)u * B + threadIdx.x) * VE);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                E e[VE];
+                Ld::template dec<VB>(w[u], e);
+                T::add_vec(acc[u], e, tlo + ((int64_t)u * B + threadIdx.x) * VE);
+            }
+            continue;
+        }
+        const int64_t lo = tlo > P0 ? tlo : P0, hi = thi < P1 ? thi : P1;
+        if (cend >= hi) {
+            ctx.masked(acc, tlo, lo, hi);
+            continue;
+        }
+        // segment cs ends inside this tile
+        ctx.masked(acc, tlo, lo, cend);
+        emit(cs, acc);
+        __syncthreads();
+        if (threadIdx.x == 0) s_i64 = sg.find(cs + 1, hi - 1);
+        __syncthreads();
+        const int64_t ns = s_i64;
+        // segments lying wholly inside the tile: short ones one per warp ...
+        for (int64_t s = cs + 1 + warp; s < ns; s += nwarps) {
+            const int64_t sb = sg.begin(s), se = sg.end(s);
+            if (se == sb || se - sb > kSmallSeg) continue;
+            Acc wa = T::init();
+            int64_t p = sb + lane;
+            for (; p + 96 < se; p += 128) {
+                const E v0 = Ld::one(x, p), v1 = Ld::one(x, p + 32), v2 = Ld::one(x, p + 64), v3 = Ld::one(x, p + 96);
+                T::add(wa, v0, p);
+                T::add(wa, v1, p + 32);
+                T::add(wa, v2, p + 64);
+                T::add(wa, v3, p + 96);
+            }
+            for (; p < se; p += 32) T::add(wa, Ld::one(x, p), p);
+            const Part q = T::warp_reduce(T::to_part(wa));
+            if (lane == 0) {
+                T::store(a.out, s, q, f64);
+                T::store_aux(a.argidx, a.aux, s, q, sb);
+            }
+        }
+        // ... long ones with the whole block
+        for (int64_t s = cs + 1; s < ns; s++) {
+            const int64_t sb = sg.begin(s), se = sg.end(s);
+            if (se - sb <= kSmallSeg) continue;
+            Acc ba_[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) ba_[u] = T::init();
+            ctx.masked(ba_, tlo, sb, se);
+            const Part q = block_combine<T>(fold<T, U>(ba_));
+            if (threadIdx.x == 0) {
+                T::store(a.out, s, q, f64);
+                T::store_aux(a.argidx, a.aux, s, q, sb);
+            }
+        }
+        cs = ns;
+        ctx.masked(acc, tlo, sg.begin(ns), hi);
+    }
+    emit(cs, acc);
+}
+
+}  // namespace pr

@@ -1,0 +1,55 @@
+// Launchers and registration helpers, included by the instantiation units.
+#pragma once
+#include "kernels.cuh"
+#include "registry.h"
+
+namespace pr {
+
+template <class T, int U, int VB>
+cudaError_t launch_reduce(const ReduceArgs& a, int grid, int block, cudaStream_t st) {
+    k_reduce<T, U, VB><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T, int U, int VB>
+cudaError_t launch_segmented(const SegArgs& a, int grid, int block, cudaStream_t st) {
+    k_segmented<T, U, VB><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_combine(const char* parts, int count, void* out, int out_f64, cudaStream_t st) {
+    k_combine_parts<T><<<1, 256, 0, st>>>(parts, count, out, out_f64);
+    return cudaGetLastError();
+}
+
+template <class T, int U, int VB>
+void reg_one(uint8_t dtype, uint8_t op, uint8_t prec, uint8_t aux, bool plain, bool seg) {
+    if (plain) {
+        reg_add(KernelKey{K_REDUCE, dtype, op, prec, aux, (uint8_t)U, (uint8_t)VB},
+                KernelEntry{reinterpret_cast<const void*>(&k_reduce<T, U, VB>),
+                            reinterpret_cast<void*>(&launch_reduce<T, U, VB>)});
+    }
+    if (seg) {
+        reg_add(KernelKey{K_SEGMENTED, dtype, op, prec, aux, (uint8_t)U, (uint8_t)VB},
+                KernelEntry{reinterpret_cast<const void*>(&k_segmented<T, U, VB>),
+                            reinterpret_cast<void*>(&launch_segmented<T, U, VB>)});
+    }
+}
+
+// Register every (unroll, vector width) of one trait; plain-reduce traits
+// also get the chunk-partial combiner used by the host-memory path.
+template <class T>
+void reg_family(uint8_t dtype, uint8_t op, uint8_t prec, uint8_t aux, bool plain, bool seg) {
+    reg_one<T, 2, 16>(dtype, op, prec, aux, plain, seg);
+    reg_one<T, 2, 32>(dtype, op, prec, aux, plain, seg);
+    reg_one<T, 4, 16>(dtype, op, prec, aux, plain, seg);
+    reg_one<T, 4, 32>(dtype, op, prec, aux, plain, seg);
+    if (plain) {
+        reg_add(KernelKey{K_COMBINE, dtype, op, prec, aux, 0, 0},
+                KernelEntry{reinterpret_cast<const void*>(&k_combine_parts<T>),
+                            reinterpret_cast<void*>(&launch_combine<T>)});
+    }
+}
+
+}  // namespace pr

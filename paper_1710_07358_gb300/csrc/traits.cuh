@@ -1,0 +1,749 @@
+// Combiner traits.  A trait describes one (element type, combiner, precision)
+// of the reduction x_0 (x) ... (x) x_{n-1} (Section 1.1):
+//
+//   Ld        element loader: storage type In, compute type E, vector decode
+//   Acc       per-thread accumulator (the "private variable" of Section 2.3)
+//   Part      value exchanged between threads and blocks
+//   init / add / add_vec    identity and accumulation of elements
+//   to_part / part_init / combine   the associative (and, bit for bit,
+//             commutative) combine used by the warp, block and grid stages
+//   warp_reduce               butterfly shuffle or redux.sync
+//   store / store_aux         final result (and argidx / product aux)
+//
+// Every combine is commutative bit for bit, so the butterfly leaves the same
+// value in every lane; all association orders are fixed by the launch
+// configuration, which makes results run-to-run deterministic.
+#pragma once
+#include <cstdint>
+#include <cuda_fp16.h>
+#include "common.cuh"
+#include "../../include/pr.h"
+
+namespace pr {
+
+// ------------------------------------------------------------------------
+// Element loaders
+// ------------------------------------------------------------------------
+
+struct LdF32 {
+    using In = float;
+    using E = float;
+    static constexpr int ES = 4;
+    template <int VB>
+    __device__ __forceinline__ static void dec(const Words<VB>& w, E (&e)[VB / ES]) {
+#pragma unroll
+        for (int k = 0; k < VB / 4; k++) e[k] = __uint_as_float(w.w[k]);
+    }
+    __device__ __forceinline__ static E one(const In* x, int64_t i) { return __ldg(x + i); }
+};
+
+// bfloat16 is the high half of a binary32: widening is a shift.
+struct LdBF16 {
+    using In = uint16_t;
+    using E = float;
+    static constexpr int ES = 2;
+    template <int VB>
+    __device__ __forceinline__ static void dec(const Words<VB>& w, E (&e)[VB / ES]) {
+#pragma unroll
+        for (int k = 0; k < VB / 4; k++) {
+            e[2 * k] = __uint_as_float(w.w[k] << 16);
+            e[2 * k + 1] = __uint_as_float(w.w[k] & 0xffff0000u);
+        }
+    }
+    __device__ __forceinline__ static E one(const In* x, int64_t i) {
+        return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(x) + i) << 16);
+    }
+};
+
+struct LdF16 {
+    using In = uint16_t;
+    using E = float;
+    static constexpr int ES = 2;
+    template <int VB>
+    __device__ __forceinline__ static void dec(const Words<VB>& w, E (&e)[VB / ES]) {
+#pragma unroll
+        for (int k = 0; k < VB / 4; k++) {
+            __half2 h;
+            memcpy(&h, &w.w[k], 4);
+            float2 f = __half22float2(h);
+            e[2 * k] = f.x;
+            e[2 * k + 1] = f.y;
+        }
+    }
+    __device__ __forceinline__ static E one(const In* x, int64_t i) {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(x) + i)));
+    }
+};
+
+struct LdF64 {
+    using In = double;
+    using E = double;
+    static constexpr int ES = 8;
+    template <int VB>
+    __device__ __forceinline__ static void dec(const Words<VB>& w, E (&e)[VB / ES]) {
+#pragma unroll
+        for (int k = 0; k < VB / 8; k++) e[k] = __hiloint2double((int)w.w[2 * k + 1], (int)w.w[2 * k]);
+    }
+    __device__ __forceinline__ static E one(const In* x, int64_t i) { return __ldg(x + i); }
+};
+
+struct LdI32 {
+    using In = int32_t;
+    using E = int32_t;
+    static constexpr int ES = 4;
+    template <int VB>
+    __device__ __forceinline__ static void dec(const Words<VB>& w, E (&e)[VB / ES]) {
+#pragma unroll
+        for (int k = 0; k < VB / 4; k++) e[k] = (int32_t)w.w[k];
+    }
+    __device__ __forceinline__ static E one(const In* x, int64_t i) { return __ldg(x + i); }
+};
+
+struct LdU32 {
+    using In = uint32_t;
+    using E = uint32_t;
+    static constexpr int ES = 4;
+    template <int VB>
+    __device__ __forceinline__ static void dec(const Words<VB>& w, E (&e)[VB / ES]) {
+#pragma unroll
+        for (int k = 0; k < VB / 4; k++) e[k] = w.w[k];
+    }
+    __device__ __forceinline__ static E one(const In* x, int64_t i) { return __ldg(x + i); }
+};
+
+// int64 is handled as uint64 bit patterns (two's-complement wrap-around).
+struct LdI64 {
+    using In = int64_t;
+    using E = uint64_t;
+    static constexpr int ES = 8;
+    template <int VB>
+    __device__ __forceinline__ static void dec(const Words<VB>& w, E (&e)[VB / ES]) {
+#pragma unroll
+        for (int k = 0; k < VB / 8; k++) e[k] = ((uint64_t)w.w[2 * k + 1] << 32) | w.w[2 * k];
+    }
+    __device__ __forceinline__ static E one(const In* x, int64_t i) {
+        return (uint64_t)__ldg(reinterpret_cast<const long long*>(x) + i);
+    }
+};
+
+// Output writers for float-valued results.
+__device__ __forceinline__ void put_f32(void* out, int64_t i, float v) { static_cast<float*>(out)[i] = v; }
+__device__ __forceinline__ void put_f64(void* out, int64_t i, double v) { static_cast<double*>(out)[i] = v; }
+
+// ------------------------------------------------------------------------
+// SUM
+// ------------------------------------------------------------------------
+
+// Float sum with an fp32 per-thread accumulator; PartT = float (PLAIN) or
+// double (FP64_COMBINE: cross-thread / cross-block combine in fp64).
+template <class Ld_, class PartT>
+struct SumF {
+    using Ld = Ld_;
+    using E = typename Ld::E;
+    using Acc = float;
+    using Part = PartT;
+    static constexpr bool kIdx = false;
+    __device__ __forceinline__ static Acc init() { return 0.f; }
+    template <int K>
+    __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t) {
+        float t[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) t[k] = e[k];
+#pragma unroll
+        for (int s = 1; s < K; s <<= 1)
+#pragma unroll
+            for (int k = 0; k + s < K; k += 2 * s) t[k] = t[k] + t[k + s];
+        a = a + t[0];
+    }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t) { a = a + v; }
+    __device__ __forceinline__ static Part to_part(const Acc& a) { return (Part)a; }
+    __device__ __forceinline__ static Part part_init() { return (Part)0; }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return a + b; }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<SumF>(p); }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) {
+        if (f64) put_f64(out, i, (double)p); else put_f32(out, i, (float)p);
+    }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
+        store(out, i, part_init(), f64);
+    }
+};
+
+// Neumaier-compensated sum (Section 1.1, second footnote: Kahan-style
+// compensation).  Per thread: kLanes independent fp32 (sum, compensation)
+// pairs, element k of a vector going to lane k mod kLanes (independent
+// dependency chains); across lanes, threads and blocks: the same algorithm in
+// fp64; one rounding at the end.
+template <class Ld_>
+struct SumComp {
+    using Ld = Ld_;
+    using E = typename Ld::E;
+    static constexpr int kLanes = 4;
+    struct Acc { float s[kLanes], c[kLanes]; };
+    struct Part { double s, c; };
+    static constexpr bool kIdx = false;
+    __device__ __forceinline__ static Acc init() {
+        Acc a;
+#pragma unroll
+        for (int l = 0; l < kLanes; l++) { a.s[l] = 0.f; a.c[l] = 0.f; }
+        return a;
+    }
+    __device__ __forceinline__ static void neumaier(float& s, float& c, float v) {
+        const float t = s + v;
+        if (fabsf(s) >= fabsf(v)) c = c + ((s - t) + v);
+        else c = c + ((v - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t) { neumaier(a.s[0], a.c[0], v); }
+    template <int K>
+    __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t) {
+#pragma unroll
+        for (int k = 0; k < K; k++) neumaier(a.s[k % kLanes], a.c[k % kLanes], e[k]);
+    }
+    __device__ __forceinline__ static Part part_init() { return {0.0, 0.0}; }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) {
+        const double t = a.s + b.s;
+        const double e = fabs(a.s) >= fabs(b.s) ? (a.s - t) + b.s : (b.s - t) + a.s;
+        return {t, (a.c + b.c) + e};
+    }
+    __device__ __forceinline__ static Part to_part(const Acc& a) {
+        Part p{(double)a.s[0], (double)a.c[0]};
+#pragma unroll
+        for (int l = 1; l < kLanes; l++) p = combine(p, Part{(double)a.s[l], (double)a.c[l]});
+        return p;
+    }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<SumComp>(p); }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) {
+        // Once an infinity enters, s stays +-inf or NaN and the compensation
+        // turns NaN; the sum is then s itself.
+        const double r = isfinite(p.s) ? p.s + p.c : p.s;
+        if (f64) put_f64(out, i, r); else put_f32(out, i, (float)r);
+    }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
+        store(out, i, part_init(), f64);
+    }
+};
+
+// fp64 input, fp64 sum.
+struct SumF64 {
+    using Ld = LdF64;
+    using E = double;
+    using Acc = double;
+    using Part = double;
+    static constexpr bool kIdx = false;
+    __device__ __forceinline__ static Acc init() { return 0.0; }
+    template <int K>
+    __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t) {
+        double t[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) t[k] = e[k];
+#pragma unroll
+        for (int s = 1; s < K; s <<= 1)
+#pragma unroll
+            for (int k = 0; k + s < K; k += 2 * s) t[k] = t[k] + t[k + s];
+        a = a + t[0];
+    }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t) { a = a + v; }
+    __device__ __forceinline__ static Part to_part(const Acc& a) { return a; }
+    __device__ __forceinline__ static Part part_init() { return 0.0; }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return a + b; }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<SumF64>(p); }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool) { put_f64(out, i, p); }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
+        store(out, i, 0.0, f64);
+    }
+};
+
+// ------------------------------------------------------------------------
+// Integer and bitwise combiners (exact).  OpK: 0 sum, 1 prod, 4 and, 5 or, 6 xor
+// ------------------------------------------------------------------------
+
+template <class Ld_, class AccT, int OpK>
+struct IntOp {
+    using Ld = Ld_;
+    using E = typename Ld::E;
+    using Acc = AccT;   // uint32_t, or uint64_t (int32 sum widened, int64)
+    using Part = AccT;
+    static constexpr bool kIdx = false;
+    __device__ __forceinline__ static AccT ident() {
+        return OpK == 1 ? (AccT)1 : (OpK == 4 ? (AccT)~(AccT)0 : (AccT)0);
+    }
+    __device__ __forceinline__ static AccT widen(E v) {
+        // int32 sum: sign-extend into the 64-bit accumulator
+        if (sizeof(AccT) == 8 && sizeof(E) == 4) return (AccT)(int64_t)(int32_t)v;
+        return (AccT)v;
+    }
+    __device__ __forceinline__ static AccT op(AccT a, AccT b) {
+        switch (OpK) {
+        case 0: return a + b;
+        case 1: return a * b;
+        case 4: return a & b;
+        case 5: return a | b;
+        default: return a ^ b;
+        }
+    }
+    __device__ __forceinline__ static Acc init() { return ident(); }
+    template <int K>
+    __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t) {
+        AccT t[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) t[k] = widen(e[k]);
+#pragma unroll
+        for (int s = 1; s < K; s <<= 1)
+#pragma unroll
+            for (int k = 0; k + s < K; k += 2 * s) t[k] = op(t[k], t[k + s]);
+        a = op(a, t[0]);
+    }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t) { a = op(a, widen(v)); }
+    __device__ __forceinline__ static Part to_part(const Acc& a) { return a; }
+    __device__ __forceinline__ static Part part_init() { return ident(); }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return op(a, b); }
+    __device__ __forceinline__ static Part warp_reduce(Part p) {
+        if constexpr (sizeof(AccT) == 4 && OpK != 1) {
+            // redux.sync: one instruction for 32-bit add / and / or / xor
+            if (OpK == 0) return __reduce_add_sync(0xffffffffu, p);
+            if (OpK == 4) return __reduce_and_sync(0xffffffffu, p);
+            if (OpK == 5) return __reduce_or_sync(0xffffffffu, p);
+            return __reduce_xor_sync(0xffffffffu, p);
+        } else {
+            return warp_combine<IntOp>(p);
+        }
+    }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool) {
+        static_cast<AccT*>(out)[i] = p;
+    }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
+        store(out, i, ident(), f64);
+    }
+};
+
+// ------------------------------------------------------------------------
+// MAX / MIN through order-preserving unsigned keys
+// ------------------------------------------------------------------------
+//
+// Each value maps to an unsigned key whose unsigned order is the value order
+// (floats: -inf < ... < -0 < +0 < ... < +inf; NaN maps to the extreme key of
+// the combiner, so it propagates).  The combine is then an integer max / min
+// (redux.sync for 32-bit keys), exact and order independent.
+
+// binary32-valued elements (f32, and bf16 / f16 widened exactly to f32).
+// OutK: 0 -> float, 1 -> bfloat16 bits, 2 -> binary16 bits.
+template <class Ld_, int OutK>
+struct KeyF32 {
+    using Ld = Ld_;
+    using E = float;
+    using K = uint32_t;
+    __device__ __forceinline__ static K key(E v, bool mx) {
+        const uint32_t b = __float_as_uint(v);
+        const uint32_t k = b ^ ((uint32_t)((int32_t)b >> 31) | 0x80000000u);
+        const bool nan = (b & 0x7fffffffu) > 0x7f800000u;
+        return nan ? (mx ? 0xffffffffu : 0u) : k;
+    }
+    __device__ __forceinline__ static K ident(bool mx) { return mx ? 0x007fffffu : 0xff800000u; }
+    __device__ __forceinline__ static void put(void* out, int64_t i, K k, bool mx) {
+        const bool nan = mx ? (k == 0xffffffffu) : (k == 0u);
+        const uint32_t b = nan ? 0x7fc00000u : ((k & 0x80000000u) ? (k ^ 0x80000000u) : ~k);
+        if (OutK == 0) static_cast<uint32_t*>(out)[i] = b;
+        else if (OutK == 1) static_cast<uint16_t*>(out)[i] = nan ? (uint16_t)0x7fc0 : (uint16_t)(b >> 16);
+        else static_cast<__half*>(out)[i] = nan ? __ushort_as_half((unsigned short)0x7e00)
+                                                : __float2half_rn(__uint_as_float(b));
+    }
+};
+
+struct KeyF64 {
+    using Ld = LdF64;
+    using E = double;
+    using K = uint64_t;
+    __device__ __forceinline__ static K key(E v, bool mx) {
+        const uint64_t b = (uint64_t)__double_as_longlong(v);
+        const uint64_t k = b ^ ((uint64_t)((int64_t)b >> 63) | 0x8000000000000000ull);
+        const bool nan = (b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+        return nan ? (mx ? ~0ull : 0ull) : k;
+    }
+    __device__ __forceinline__ static K ident(bool mx) {
+        return mx ? 0x000fffffffffffffull : 0xfff0000000000000ull;
+    }
+    __device__ __forceinline__ static void put(void* out, int64_t i, K k, bool mx) {
+        const bool nan = mx ? (k == ~0ull) : (k == 0ull);
+        const uint64_t b = nan ? 0x7ff8000000000000ull
+                               : ((k & 0x8000000000000000ull) ? (k ^ 0x8000000000000000ull) : ~k);
+        static_cast<uint64_t*>(out)[i] = b;
+    }
+};
+
+struct KeyI32 {
+    using Ld = LdI32;
+    using E = int32_t;
+    using K = uint32_t;
+    __device__ __forceinline__ static K key(E v, bool) { return (uint32_t)v ^ 0x80000000u; }
+    __device__ __forceinline__ static K ident(bool mx) { return mx ? 0u : 0xffffffffu; }
+    __device__ __forceinline__ static void put(void* out, int64_t i, K k, bool) {
+        static_cast<uint32_t*>(out)[i] = k ^ 0x80000000u;
+    }
+};
+
+struct KeyU32 {
+    using Ld = LdU32;
+    using E = uint32_t;
+    using K = uint32_t;
+    __device__ __forceinline__ static K key(E v, bool) { return v; }
+    __device__ __forceinline__ static K ident(bool mx) { return mx ? 0u : 0xffffffffu; }
+    __device__ __forceinline__ static void put(void* out, int64_t i, K k, bool) { static_cast<uint32_t*>(out)[i] = k; }
+};
+
+struct KeyI64 {
+    using Ld = LdI64;
+    using E = uint64_t;
+    using K = uint64_t;
+    __device__ __forceinline__ static K key(E v, bool) { return v ^ 0x8000000000000000ull; }
+    __device__ __forceinline__ static K ident(bool mx) { return mx ? 0ull : ~0ull; }
+    __device__ __forceinline__ static void put(void* out, int64_t i, K k, bool) {
+        static_cast<uint64_t*>(out)[i] = k ^ 0x8000000000000000ull;
+    }
+};
+
+template <class Key, bool MX>
+struct MaxMin {
+    using Ld = typename Key::Ld;
+    using E = typename Key::E;
+    using K = typename Key::K;
+    using Acc = K;
+    using Part = K;
+    static constexpr bool kIdx = false;
+    __device__ __forceinline__ static K pick(K a, K b) { return MX ? (a > b ? a : b) : (a < b ? a : b); }
+    __device__ __forceinline__ static Acc init() { return Key::ident(MX); }
+    template <int N>
+    __device__ __forceinline__ static void add_vec(Acc& a, const typename Ld::E (&e)[N], int64_t) {
+        K t[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) t[k] = Key::key((E)e[k], MX);
+#pragma unroll
+        for (int s = 1; s < N; s <<= 1)
+#pragma unroll
+            for (int k = 0; k + s < N; k += 2 * s) t[k] = pick(t[k], t[k + s]);
+        a = pick(a, t[0]);
+    }
+    __device__ __forceinline__ static void add(Acc& a, typename Ld::E v, int64_t) { a = pick(a, Key::key((E)v, MX)); }
+    __device__ __forceinline__ static Part to_part(const Acc& a) { return a; }
+    __device__ __forceinline__ static Part part_init() { return Key::ident(MX); }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return pick(a, b); }
+    __device__ __forceinline__ static Part warp_reduce(Part p) {
+        if constexpr (sizeof(K) == 4) {
+            return MX ? __reduce_max_sync(0xffffffffu, p) : __reduce_min_sync(0xffffffffu, p);
+        } else {
+            return warp_combine<MaxMin>(p);
+        }
+    }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool) { Key::put(out, i, p, MX); }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
+        store(out, i, part_init(), f64);
+    }
+};
+
+// binary32-valued MAX / MIN (f32; bf16 / f16 widened exactly to f32): the
+// per-thread accumulation uses max.NaN / min.NaN, one instruction per element,
+// which propagate NaN and order -0 below +0 in either operand order -- the
+// same semantics as the order-preserving keys, to which the accumulator is
+// converted for the warp / block / grid combine.
+template <class Ld_, int OutK, bool MX>
+struct MaxMinF {
+    using Ld = Ld_;
+    using E = float;
+    using Key = KeyF32<Ld_, OutK>;
+    using Acc = float;
+    using Part = uint32_t;
+    static constexpr bool kIdx = false;
+    __device__ __forceinline__ static float f(float a, float b) {
+        float r;
+        if (MX) asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+        else asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+        return r;
+    }
+    __device__ __forceinline__ static Acc init() { return MX ? -INFINITY : INFINITY; }
+    template <int N>
+    __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[N], int64_t) {
+        float t[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) t[k] = e[k];
+#pragma unroll
+        for (int s = 1; s < N; s <<= 1)
+#pragma unroll
+            for (int k = 0; k + s < N; k += 2 * s) t[k] = f(t[k], t[k + s]);
+        a = f(a, t[0]);
+    }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t) { a = f(a, v); }
+    __device__ __forceinline__ static Part to_part(const Acc& a) { return Key::key(a, MX); }
+    __device__ __forceinline__ static Part part_init() { return Key::ident(MX); }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) {
+        return MX ? (a > b ? a : b) : (a < b ? a : b);
+    }
+    __device__ __forceinline__ static Part warp_reduce(Part p) {
+        return MX ? __reduce_max_sync(0xffffffffu, p) : __reduce_min_sync(0xffffffffu, p);
+    }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool) { Key::put(out, i, p, MX); }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
+        store(out, i, part_init(), f64);
+    }
+};
+
+// Extremum plus the index of its first occurrence: ties go to the smaller
+// index, so the combine is order independent and the result unique.
+template <class Key, bool MX>
+struct ArgExt {
+    using Ld = typename Key::Ld;
+    using E = typename Key::E;
+    using K = typename Key::K;
+    struct Acc { K key; int64_t idx; };
+    using Part = Acc;
+    static constexpr bool kIdx = true;
+    static constexpr int64_t kNone = INT64_MAX;
+    __device__ __forceinline__ static bool better(K ka, int64_t ia, K kb, int64_t ib) {
+        return (MX ? ka > kb : ka < kb) || (ka == kb && ia < ib);
+    }
+    __device__ __forceinline__ static Acc init() { Acc a{}; a.key = Key::ident(MX); a.idx = kNone; return a; }
+    __device__ __forceinline__ static void add(Acc& a, typename Ld::E v, int64_t i) {
+        const K k = Key::key((E)v, MX);
+        if (better(k, i, a.key, a.idx)) { a.key = k; a.idx = i; }
+    }
+    template <int N>
+    __device__ __forceinline__ static void add_vec(Acc& a, const typename Ld::E (&e)[N], int64_t i0) {
+#pragma unroll
+        for (int k = 0; k < N; k++) add(a, e[k], i0 + k);
+    }
+    __device__ __forceinline__ static Part to_part(const Acc& a) { return a; }
+    __device__ __forceinline__ static Part part_init() { return init(); }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) {
+        return better(b.key, b.idx, a.key, a.idx) ? b : a;
+    }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<ArgExt>(p); }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool) { Key::put(out, i, p.key, MX); }
+    __device__ __forceinline__ static void store_aux(int64_t* argidx, pr_prod_aux*, int64_t i, const Part& p,
+                                                     int64_t seg_begin) {
+        if (argidx) argidx[i] = p.idx == kNone ? -1 : p.idx - seg_begin;
+    }
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t* argidx, pr_prod_aux*) {
+        store(out, i, part_init(), f64);
+        if (argidx) argidx[i] = -1;
+    }
+};
+
+// ------------------------------------------------------------------------
+// PROD
+// ------------------------------------------------------------------------
+
+// fp32 product (f32 input; bf16 / f16 widened to fp32).
+template <class Ld_>
+struct ProdF {
+    using Ld = Ld_;
+    using E = typename Ld::E;
+    using Acc = float;
+    using Part = float;
+    static constexpr bool kIdx = false;
+    static constexpr bool kOutF64 = false;
+    __device__ __forceinline__ static Acc init() { return 1.f; }
+    template <int K>
+    __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t) {
+        float t[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) t[k] = e[k];
+#pragma unroll
+        for (int s = 1; s < K; s <<= 1)
+#pragma unroll
+            for (int k = 0; k + s < K; k += 2 * s) t[k] = t[k] * t[k + s];
+        a = a * t[0];
+    }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t) { a = a * v; }
+    __device__ __forceinline__ static Part to_part(const Acc& a) { return a; }
+    __device__ __forceinline__ static Part part_init() { return 1.f; }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return a * b; }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<ProdF>(p); }
+    __device__ __forceinline__ static double value(const Part& p) { return (double)p; }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool) { put_f32(out, i, p); }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
+        store(out, i, 1.f, f64);
+    }
+};
+
+// fp64 product on the integer pipes.  GB300's fp64 units issue ~0.5e12
+// multiplies/s, slower than HBM delivers doubles (~0.9e12/s), so the combine
+// keeps a 64-bit significand m in [2^63, 2^64) and a 64-bit exponent e
+// (value = m * 2^(e-63)) and multiplies significands with four 32x32->64
+// integer multiplies, rounding the 128-bit product to nearest.  Each step
+// errs by at most 2^-64 relative (fp64: 2^-53), and there is no intermediate
+// overflow or underflow.  Zeros, infinities and NaNs are flags; the sign is
+// the xor of all signs (the IEEE rule for multiplication).
+struct ProdExt {
+    using Ld = LdF64;
+    using E = double;
+    enum : uint32_t { kNeg = 1, kZero = 2, kInf = 4, kNan = 8 };
+    struct Acc { uint64_t m; int64_t e; uint32_t f; uint32_t pad_; };
+    using Part = Acc;
+    static constexpr bool kIdx = false;
+    static constexpr bool kOutF64 = true;
+
+    // m' = round(a*b / 2^(63+adj)), a, b in [2^63, 2^64); returns m' in [2^63, 2^64).
+    __device__ __forceinline__ static uint64_t mul_sig(uint64_t a, uint64_t b, int& adj) {
+        const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+        const uint64_t p00 = (uint64_t)a0 * b0, p01 = (uint64_t)a0 * b1;
+        const uint64_t p10 = (uint64_t)a1 * b0, p11 = (uint64_t)a1 * b1;
+        const uint64_t mid = (p00 >> 32) + (uint32_t)p01 + (uint32_t)p10;
+        const uint64_t hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+        const uint32_t lo_hi = (uint32_t)mid;  // bits 32..63 of the low 64-bit word
+        const int top = (int)(hi >> 63);
+        uint64_t m = top ? hi : ((hi << 1) | (lo_hi >> 31));
+        const uint32_t rb = top ? (lo_hi >> 31) : ((lo_hi >> 30) & 1u);
+        m += rb;
+        const int ovf = (m == 0);  // rounding carried out of bit 63
+        m = ovf ? 0x8000000000000000ull : m;
+        adj = top + ovf;
+        return m;
+    }
+    __device__ __forceinline__ static Acc init() { Acc a; a.m = 0x8000000000000000ull; a.e = 0; a.f = 0; a.pad_ = 0; return a; }
+
+    // Significand b in [2^63, 2^64) and biased exponent of v (v = b * 2^(ebias - 1023 - 63)),
+    // or a neutral factor (2^63, 1023) with the class recorded in f for 0 / inf / NaN.
+    __device__ __forceinline__ static void decode(uint64_t bits, uint64_t& b, int32_t& ebias, uint32_t& f) {
+        const uint32_t ef = (uint32_t)(bits >> 52) & 0x7ffu;
+        const uint64_t mant = bits & 0x000fffffffffffffull;
+        b = (mant | 0x0010000000000000ull) << 11;
+        ebias = (int32_t)ef;
+        if (__builtin_expect(ef - 1u >= 0x7feu, 0)) {
+            if (ef == 0x7ffu) { f |= mant ? kNan : kInf; b = 0x8000000000000000ull; ebias = 1023; }
+            else if (mant == 0) { f |= kZero; b = 0x8000000000000000ull; ebias = 1023; }
+            else { const int s = __clzll((long long)mant); b = mant << s; ebias = 12 - s; }  // subnormal
+        }
+    }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t) {
+        const uint64_t bits = (uint64_t)__double_as_longlong(v);
+        a.f ^= (uint32_t)(bits >> 63);
+        uint64_t b;
+        int32_t eb;
+        decode(bits, b, eb, a.f);
+        int adj;
+        a.m = mul_sig(a.m, b, adj);
+        a.e += (int64_t)eb - 1023 + adj;
+    }
+    // A vector's factors are multiplied pairwise first, so the accumulator's
+    // dependent chain advances once per vector rather than once per element.
+    template <int K>
+    __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t) {
+        uint64_t b[K];
+        int32_t eb[K];
+        uint32_t sgn = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint64_t bits = (uint64_t)__double_as_longlong(e[k]);
+            sgn ^= (uint32_t)(bits >> 32);
+            decode(bits, b[k], eb[k], a.f);
+        }
+        a.f ^= sgn >> 31;
+#pragma unroll
+        for (int s = 1; s < K; s <<= 1)
+#pragma unroll
+            for (int k = 0; k + s < K; k += 2 * s) {
+                int adj;
+                b[k] = mul_sig(b[k], b[k + s], adj);
+                eb[k] += eb[k + s] + adj;
+            }
+        int adj;
+        a.m = mul_sig(a.m, b[0], adj);
+        a.e += (int64_t)eb[0] - 1023 * K + adj;
+    }
+    __device__ __forceinline__ static Part to_part(const Acc& a) { return a; }
+    __device__ __forceinline__ static Part part_init() { return init(); }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) {
+        Part r;
+        int adj;
+        r.m = mul_sig(a.m, b.m, adj);
+        r.e = a.e + b.e + adj;
+        r.f = ((a.f ^ b.f) & kNeg) | ((a.f | b.f) & (kZero | kInf | kNan));
+        r.pad_ = 0;
+        return r;
+    }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<ProdExt>(p); }
+    __device__ __forceinline__ static double value(const Part& p) {
+        const bool neg = p.f & kNeg;
+        if ((p.f & kNan) || ((p.f & kInf) && (p.f & kZero))) return __longlong_as_double(0x7ff8000000000000ll);
+        if (p.f & kInf) return neg ? -INFINITY : INFINITY;
+        if (p.f & kZero) return neg ? -0.0 : 0.0;
+        const double d = __ull2double_rn(p.m);
+        int64_t sh = p.e - 63;
+        sh = sh < -4000 ? -4000 : (sh > 4000 ? 4000 : sh);
+        const double r = ldexp(d, (int)sh);
+        return neg ? -r : r;
+    }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool) { put_f64(out, i, value(p)); }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
+        put_f64(out, i, 1.0);
+    }
+};
+
+// Product that also records what its gradient needs: the product of the
+// non-zero elements, the number of zeros, the first zero's index and the xor
+// of the zeros' signs.  The product itself is P_nz * (+-0) when zeros exist.
+template <class Base>
+struct ProdAux {
+    using Ld = typename Base::Ld;
+    using E = typename Ld::E;
+    struct Acc { typename Base::Acc p; int64_t zc; int64_t zi; uint32_t zsign; uint32_t pad_; };
+    struct Part { typename Base::Part p; int64_t zc; int64_t zi; uint32_t zsign; uint32_t pad_; };
+    static constexpr bool kIdx = true;
+    __device__ __forceinline__ static Acc init() { Acc a; a.p = Base::init(); a.zc = 0; a.zi = INT64_MAX; a.zsign = 0; a.pad_ = 0; return a; }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t i) {
+        if (v == (E)0) {
+            a.zc += 1;
+            a.zi = i < a.zi ? i : a.zi;
+            a.zsign ^= (uint32_t)(signbit(v) != 0);
+        } else {
+            Base::add(a.p, v, i);
+        }
+    }
+    template <int K>
+    __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t i0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) add(a, e[k], i0 + k);
+    }
+    __device__ __forceinline__ static Part to_part(const Acc& a) {
+        Part r; r.p = Base::to_part(a.p); r.zc = a.zc; r.zi = a.zi; r.zsign = a.zsign; r.pad_ = 0; return r;
+    }
+    __device__ __forceinline__ static Part part_init() { return to_part(init()); }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) {
+        Part r;
+        r.p = Base::combine(a.p, b.p);
+        r.zc = a.zc + b.zc;
+        r.zi = a.zi < b.zi ? a.zi : b.zi;
+        r.zsign = a.zsign ^ b.zsign;
+        r.pad_ = 0;
+        return r;
+    }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<ProdAux>(p); }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) {
+        const double pnz = Base::value(p.p);
+        const double v = p.zc > 0 ? pnz * (p.zsign ? -0.0 : 0.0) : pnz;
+        if (Base::kOutF64) put_f64(out, i, v); else put_f32(out, i, (float)v);
+    }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux* aux, int64_t i, const Part& p,
+                                                     int64_t seg_begin) {
+        if (aux) {
+            pr_prod_aux r;
+            r.p_nz = Base::value(p.p);
+            r.zero_count = p.zc;
+            r.first_zero = p.zc > 0 ? p.zi - seg_begin : -1;
+            aux[i] = r;
+        }
+    }
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux* aux) {
+        const Part e = part_init();
+        store(out, i, e, f64);
+        store_aux(nullptr, aux, i, e, 0);
+    }
+};
+
+}  // namespace pr

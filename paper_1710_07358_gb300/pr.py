@@ -1,0 +1,359 @@
+"""Python binding of libpr.so (the C ABI in include/pr.h).
+
+Two layers, both argument marshalling only:
+  * ``pr_*`` functions with the C names and signatures (raw integers for
+    pointers and stream handles), returning the status code;
+  * tensor helpers (``reduce``, ``segmented_reduce``, ``reduce_rows``,
+    ``reduce_backward``, ``reduce_host``) that take torch tensors, pass their
+    device pointers and torch's current stream, allocate outputs with torch
+    and raise ``PrError`` on a non-OK status.
+
+Every reduction runs in the library's CUDA kernels; if libpr.so is missing the
+first call raises.  There is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpr.so")
+
+DTYPES = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3, "i32": 4, "u32": 5, "i64": 6}
+OPS = {"sum": 0, "prod": 1, "max": 2, "min": 3, "and": 4, "or": 5, "xor": 6}
+PRECISIONS = {"plain": 0, "compensated": 1, "fp64_combine": 2}
+KINDS = {"reduce": 0, "segmented": 1, "backward": 2}
+STATUS = {0: "PR_OK", 1: "PR_ERR_INVALID", 2: "PR_ERR_UNSUPPORTED", 3: "PR_ERR_CUDA",
+          4: "PR_ERR_TIMEOUT", 5: "PR_ERR_NOMEM"}
+ELEM_SIZE = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "i32": 4, "u32": 4, "i64": 8}
+
+
+class pr_config(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("unroll", ctypes.c_int32), ("vec_bytes", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class pr_prod_aux(ctypes.Structure):
+    _fields_ = [("p_nz", ctypes.c_double), ("zero_count", ctypes.c_int64), ("first_zero", ctypes.c_int64)]
+
+
+class PrError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+_P, _I64, _I32, _I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+_SIGS = {
+    "pr_reduce": [_P, _I64, _I, _I, _P, _P],
+    "pr_reduce_ex": [_P, _I64, _I, _I, _I, _I, _P, _P],
+    "pr_segmented_reduce": [_P, _P, _I64, _I, _I, _P, _P],
+    "pr_segmented_reduce_aux": [_P, _P, _I64, _I, _I, _I, _P, _P, _P, _P],
+    "pr_reduce_rows": [_P, _I64, _I64, _I, _I, _I, _P, _P, _P, _P],
+    "pr_reduce_backward": [_I, _I, _P, _I64, _I64, _P, _P, _P, _P, _P],
+    "pr_reduce_host": [_P, _I64, _I, _I, _P, _P],
+    "pr_prepare": [_P],
+    "pr_last_device_error": [_P, ctypes.POINTER(_I32)],
+    "pr_get_config": [_I, _I, _I, _I, _I64, ctypes.POINTER(pr_config)],
+    "pr_set_config": [_I, _I, _I, _I, _I64, ctypes.POINTER(pr_config)],
+    "pr_autotune": [_I, _P, _I64, _P, _I64, _I, _I, _I, _P, ctypes.POINTER(pr_config)],
+    "pr_tune_save": [ctypes.c_char_p],
+    "pr_tune_load": [ctypes.c_char_p],
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libpr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpr.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes, f.restype = args, _I
+        L.pr_out_dtype.argtypes, L.pr_out_dtype.restype = [_I, _I], _I
+        L.pr_status_string.argtypes, L.pr_status_string.restype = [_I], ctypes.c_char_p
+        L.pr_last_error_message.argtypes, L.pr_last_error_message.restype = [], ctypes.c_char_p
+        L.pr_version.argtypes, L.pr_version.restype = [], ctypes.c_char_p
+        _lib = L
+        _load_tuning(L)
+    return _lib
+
+
+TUNING_PATH = os.path.join(_HERE, "tuning", "gb300.json")
+
+
+def _load_tuning(L):
+    """Load the shipped launch-configuration table when a GPU is present (the
+    library checks that the table was made on a GPU of the same name)."""
+    if os.environ.get("PR_NO_TUNING") or not os.path.exists(TUNING_PATH):
+        return
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return
+    except ImportError:
+        return
+    L.pr_tune_load(TUNING_PATH.encode())
+
+
+# ---------------------------------------------------------------------------
+# C names (raw arguments, status returned)
+# ---------------------------------------------------------------------------
+
+def pr_reduce(x, n, dtype, op, out, stream):
+    return lib().pr_reduce(x, n, dtype, op, out, stream)
+
+
+def pr_reduce_ex(x, n, dtype, op, precision, out_dtype, out, stream):
+    return lib().pr_reduce_ex(x, n, dtype, op, precision, out_dtype, out, stream)
+
+
+def pr_segmented_reduce(x, offsets, nseg, dtype, op, out, stream):
+    return lib().pr_segmented_reduce(x, offsets, nseg, dtype, op, out, stream)
+
+
+def pr_segmented_reduce_aux(x, offsets, nseg, dtype, op, precision, out, argidx, aux, stream):
+    return lib().pr_segmented_reduce_aux(x, offsets, nseg, dtype, op, precision, out, argidx, aux, stream)
+
+
+def pr_reduce_rows(x, rows, cols, dtype, op, precision, out, argidx, aux, stream):
+    return lib().pr_reduce_rows(x, rows, cols, dtype, op, precision, out, argidx, aux, stream)
+
+
+def pr_reduce_backward(op, dtype, x, rows, cols, grad_out, argidx, aux, grad_in, stream):
+    return lib().pr_reduce_backward(op, dtype, x, rows, cols, grad_out, argidx, aux, grad_in, stream)
+
+
+def pr_reduce_host(host_x, n, dtype, op, host_out, stream):
+    return lib().pr_reduce_host(host_x, n, dtype, op, host_out, stream)
+
+
+def pr_prepare(stream):
+    return lib().pr_prepare(stream)
+
+
+def pr_last_device_error(stream, code_ref):
+    return lib().pr_last_device_error(stream, code_ref)
+
+
+def pr_out_dtype(dtype, op):
+    return lib().pr_out_dtype(dtype, op)
+
+
+def pr_status_string(status):
+    return lib().pr_status_string(status).decode()
+
+
+def pr_last_error_message():
+    return lib().pr_last_error_message().decode()
+
+
+def pr_version():
+    return lib().pr_version().decode()
+
+
+def pr_get_config(kind, dtype, op, precision, n, cfg_ref):
+    return lib().pr_get_config(kind, dtype, op, precision, n, cfg_ref)
+
+
+def pr_set_config(kind, dtype, op, precision, n, cfg_ref):
+    return lib().pr_set_config(kind, dtype, op, precision, n, cfg_ref)
+
+
+def pr_autotune(kind, x, n, offsets, nseg, dtype, op, precision, stream, best_ref):
+    return lib().pr_autotune(kind, x, n, offsets, nseg, dtype, op, precision, stream, best_ref)
+
+
+def pr_tune_save(path):
+    return lib().pr_tune_save(path.encode() if isinstance(path, str) else path)
+
+
+def pr_tune_load(path):
+    return lib().pr_tune_load(path.encode() if isinstance(path, str) else path)
+
+
+def check(status):
+    if status != 0:
+        raise PrError(status, pr_last_error_message())
+
+
+# ---------------------------------------------------------------------------
+# Tensor helpers
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_name(t) -> str:
+    torch = _torch()
+    m = {torch.float32: "f32", torch.float16: "f16", torch.bfloat16: "bf16", torch.float64: "f64",
+         torch.int32: "i32", torch.int64: "i64"}
+    if hasattr(torch, "uint32"):
+        m[torch.uint32] = "u32"
+    if t.dtype not in m:
+        raise TypeError("unsupported tensor dtype %s" % t.dtype)
+    return m[t.dtype]
+
+
+def torch_dtype(name: str):
+    torch = _torch()
+    return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16, "f64": torch.float64,
+            "i32": torch.int32, "i64": torch.int64, "u32": getattr(torch, "uint32", None)}[name]
+
+
+def out_dtype_name(dtype: str, op: str) -> str:
+    if dtype in ("f16", "bf16"):
+        return dtype if op in ("max", "min") else "f32"
+    if dtype == "i32" and op == "sum":
+        return "i64"
+    return dtype
+
+
+def _stream(t, stream=None):
+    torch = _torch()
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def _ptr(t):
+    return t.data_ptr() if t is not None else None
+
+
+def reduce(x, op: str, precision: str = "plain", out_dtype: str | None = None, out=None, stream=None):
+    """0-d tensor holding the reduction of every element of the CUDA tensor x."""
+    torch = _torch()
+    if not x.is_cuda:
+        raise ValueError("reduce() needs a CUDA tensor; use reduce_host() for host memory")
+    if not x.is_contiguous():
+        raise ValueError("x must be contiguous")
+    d = dtype_name(x)
+    od = out_dtype or out_dtype_name(d, op)
+    if out is None:
+        out = torch.empty((), dtype=torch_dtype(od), device=x.device)
+    check(pr_reduce_ex(_ptr(x), x.numel(), DTYPES[d], OPS[op], PRECISIONS[precision], DTYPES[od],
+                       _ptr(out), _stream(x, stream)))
+    return out
+
+
+def segmented_reduce(x, offsets, op: str, precision: str = "plain", argidx: bool = False,
+                     aux: bool = False, stream=None):
+    """Per-segment reductions of x[offsets[s]:offsets[s+1]] (offsets: int64 CUDA tensor).
+
+    Returns out, or (out, argidx) / (out, aux) when requested; aux is an
+    int8 tensor of nseg * 24 bytes (pr_prod_aux records), see prod_aux_fields()."""
+    torch = _torch()
+    d = dtype_name(x)
+    nseg = offsets.numel() - 1
+    if offsets.dtype != torch.int64 or not offsets.is_cuda or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous int64 CUDA tensor")
+    out = torch.empty(max(nseg, 0), dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
+    ai = torch.empty(max(nseg, 0), dtype=torch.int64, device=x.device) if argidx else None
+    ax = torch.empty(max(nseg, 0) * 24, dtype=torch.int8, device=x.device) if aux else None
+    check(pr_segmented_reduce_aux(_ptr(x), _ptr(offsets), nseg, DTYPES[d], OPS[op], PRECISIONS[precision],
+                                  _ptr(out), _ptr(ai), _ptr(ax), _stream(x, stream)))
+    if argidx:
+        return out, ai
+    if aux:
+        return out, ax
+    return out
+
+
+def reduce_rows(x, op: str, precision: str = "plain", argidx: bool = False, aux: bool = False, stream=None):
+    """Reduce a contiguous [rows, cols] CUDA tensor along its last dimension."""
+    torch = _torch()
+    if x.dim() != 2 or not x.is_contiguous():
+        raise ValueError("reduce_rows needs a contiguous 2-D tensor")
+    d = dtype_name(x)
+    rows, cols = x.shape
+    out = torch.empty(rows, dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
+    ai = torch.empty(rows, dtype=torch.int64, device=x.device) if argidx else None
+    ax = torch.empty(rows * 24, dtype=torch.int8, device=x.device) if aux else None
+    check(pr_reduce_rows(_ptr(x), rows, cols, DTYPES[d], OPS[op], PRECISIONS[precision], _ptr(out), _ptr(ai),
+                         _ptr(ax), _stream(x, stream)))
+    if argidx:
+        return out, ai
+    if aux:
+        return out, ax
+    return out
+
+
+def prod_aux_fields(aux):
+    """(p_nz float64, zero_count int64, first_zero int64) tensors from an aux byte tensor."""
+    torch = _torch()
+    rec = aux.view(torch.int64).view(-1, 3)
+    return rec[:, 0].view(torch.float64), rec[:, 1], rec[:, 2]
+
+
+def reduce_backward(op: str, x, grad_out, argidx=None, aux=None, out=None, stream=None):
+    """grad_in [rows, cols] for a row reduction of x (see pr_reduce_backward)."""
+    torch = _torch()
+    d = dtype_name(grad_out)
+    rows, cols = x.shape
+    gi = out if out is not None else torch.empty((rows, cols), dtype=grad_out.dtype, device=grad_out.device)
+    xp = _ptr(x) if op == "prod" else None
+    check(pr_reduce_backward(OPS[op], DTYPES[d], xp, rows, cols, _ptr(grad_out.contiguous()), _ptr(argidx),
+                             _ptr(aux), _ptr(gi), _stream(grad_out, stream)))
+    return gi
+
+
+def reduce_host(x, op: str, stream=None):
+    """Reduce a host tensor (pinned for full speed) on the current GPU; returns a Python number."""
+    torch = _torch()
+    if x.is_cuda or not x.is_contiguous():
+        raise ValueError("reduce_host needs a contiguous host tensor")
+    import numpy as np
+    d = dtype_name(x)
+    od = out_dtype_name(d, op)
+    res = np.zeros(1, dtype={"f32": np.float32, "f64": np.float64, "i32": np.int32, "u32": np.uint32,
+                             "i64": np.int64, "f16": np.uint16, "bf16": np.uint16}[od])
+    st = torch.cuda.current_stream().cuda_stream if stream is None else _stream(x, stream)
+    check(pr_reduce_host(_ptr(x), x.numel(), DTYPES[d], OPS[op], res.ctypes.data, st))
+    if od == "f16":
+        return float(res.view(np.float16)[0])
+    if od == "bf16":
+        return float((res.astype(np.uint32) << 16).view(np.float32)[0])
+    return res[0].item()
+
+
+def prepare(stream=None):
+    torch = _torch()
+    st = torch.cuda.current_stream().cuda_stream if stream is None else _stream(None, stream)
+    check(pr_prepare(st))
+
+
+def last_device_error(stream=None) -> int:
+    torch = _torch()
+    st = torch.cuda.current_stream().cuda_stream if stream is None else _stream(None, stream)
+    code = ctypes.c_int32(0)
+    check(pr_last_device_error(st, ctypes.byref(code)))
+    return code.value
+
+
+def get_config(kind: str, dtype: str, op: str, precision: str = "plain", n: int = 1) -> dict:
+    c = pr_config()
+    check(pr_get_config(KINDS[kind], DTYPES[dtype], OPS[op], PRECISIONS[precision], n, ctypes.byref(c)))
+    return c.as_dict()
+
+
+def set_config(kind: str, dtype: str, op: str, precision: str, n: int, cfg: dict):
+    c = pr_config(**cfg)
+    check(pr_set_config(KINDS[kind], DTYPES[dtype], OPS[op], PRECISIONS[precision], n, ctypes.byref(c)))
+
+
+def autotune(kind: str, x, op: str, precision: str = "plain", offsets=None, stream=None) -> dict:
+    d = dtype_name(x)
+    c = pr_config()
+    nseg = offsets.numel() - 1 if offsets is not None else 0
+    check(pr_autotune(KINDS[kind], _ptr(x), x.numel(), _ptr(offsets), nseg, DTYPES[d], OPS[op],
+                      PRECISIONS[precision], _stream(x, stream), ctypes.byref(c)))
+    return c.as_dict()

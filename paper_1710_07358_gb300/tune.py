@@ -1,0 +1,89 @@
+"""Build the launch-configuration table for this GPU with the library's autotuner.
+
+For every (dtype, combiner, precision) of the plain reduction and a range of
+size buckets, and for the segmented reduction on log-uniform segments, this
+calls pr_autotune on synthetic data (timing every block size / blocks-per-SM /
+unroll / vector-width candidate with CUDA events) and saves the winners with
+pr_tune_save.  The binding loads the table for the current GPU on first use.
+
+    python -m paper_1710_07358_gb300.tune [--out PATH] [--sizes 20,24,28] [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import os
+
+from . import pr
+
+DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "gb300.json")
+
+PLAIN = [("f32", "sum"), ("f32", "prod"), ("f32", "max"), ("f32", "min"),
+         ("f16", "sum"), ("f16", "prod"), ("f16", "max"), ("f16", "min"),
+         ("bf16", "sum"), ("bf16", "prod"), ("bf16", "max"), ("bf16", "min"),
+         ("f64", "sum"), ("f64", "prod"), ("f64", "max"), ("f64", "min")] + \
+        [(d, o) for d in ("i32", "u32", "i64") for o in ("sum", "prod", "max", "min", "and", "or", "xor")]
+PRECISE = [("f32", "compensated"), ("f32", "fp64_combine"), ("f16", "compensated"), ("f16", "fp64_combine"),
+           ("bf16", "compensated"), ("bf16", "fp64_combine")]
+
+
+def _data(torch, dtype, op, n, g):
+    dev = "cuda"
+    if dtype in ("f32", "f16", "bf16"):
+        if op == "prod":
+            x = 1.0 + (torch.rand(n, generator=g, device=dev) - 0.5) * 2 ** -6
+        else:
+            x = torch.rand(n, generator=g, device=dev) * 2 - 1
+        return x.to(pr.torch_dtype(dtype))
+    if dtype == "f64":
+        return torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 0.002 + 0.999
+    if dtype == "i32":
+        return torch.randint(-(1 << 20), 1 << 20, (n,), generator=g, device=dev, dtype=torch.int32)
+    if dtype == "u32":
+        return torch.randint(-(1 << 31), (1 << 31) - 1, (n,), generator=g, device=dev,
+                             dtype=torch.int32).view(torch.uint32)
+    return torch.randint(-(1 << 62), 1 << 62, (n,), generator=g, device=dev, dtype=torch.int64)
+
+
+def main():
+    import torch
+    from . import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=DEFAULT_PATH)
+    ap.add_argument("--sizes", default="20,22,24,26,28,30")
+    ap.add_argument("--quick", action="store_true", help="only 2^28 and the segmented workload")
+    args = ap.parse_args()
+    sizes = [28] if args.quick else [int(s) for s in args.sizes.split(",")]
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1)
+    for k in sizes:
+        n = 1 << k
+        for dtype, op in PLAIN:
+            if k >= 30 and dtype in ("f64", "i64"):
+                continue
+            x = _data(torch, dtype, op, n, g)
+            cfg = pr.autotune("reduce", x, op)
+            print("reduce 2^%d %s %s: %s" % (k, dtype, op, cfg), flush=True)
+            del x
+        for dtype, prec in PRECISE:
+            x = _data(torch, dtype, "sum", n, g)
+            cfg = pr.autotune("reduce", x, "sum", precision=prec)
+            print("reduce 2^%d %s sum %s: %s" % (k, dtype, prec, cfg), flush=True)
+            del x
+        torch.cuda.empty_cache()
+    vals, off = synth.segmented_workload(4096, synth.config_seed(3))
+    xv = torch.from_numpy(vals).cuda()
+    ov = torch.from_numpy(off).cuda()
+    for op in ("sum", "max", "min", "prod"):
+        cfg = pr.autotune("segmented", xv, op, offsets=ov)
+        print("segmented 4096 f32 %s: %s" % (op, cfg), flush=True)
+    for prec in ("compensated", "fp64_combine"):
+        cfg = pr.autotune("segmented", xv, "sum", precision=prec, offsets=ov)
+        print("segmented 4096 f32 sum %s: %s" % (prec, cfg), flush=True)
+    os.makedirs(os.path.dirname(args.out), exist_ok=True)
+    pr.check(pr.pr_tune_save(args.out))
+    print("saved", args.out)
+
+
+if __name__ == "__main__":
+    main()

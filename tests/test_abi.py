@@ -1,0 +1,135 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/pr.h declares, and rejects bad arguments on the host with the
+documented status before anything is enqueued."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1710_07358_gb300 import pr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+OK, INVALID, UNSUPPORTED, CUDA = 0, 1, 2, 3
+F32, F16, BF16, F64, I32, U32, I64 = range(7)
+SUM, PROD, MAX, MIN, AND, OR, XOR = range(7)
+PLAIN, COMP, F64C = range(3)
+FAKE = 0x10000      # an aligned address that is never dereferenced (validation fails first)
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(pr.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return pr.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "pr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pr_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_python_binding_mirrors_c_names():
+    for n in declared_functions():
+        assert callable(getattr(pr, n)), n
+
+
+def test_version_and_status_strings(L):
+    assert pr.pr_version().startswith("pr ")
+    for code, name in pr.STATUS.items():
+        assert pr.pr_status_string(code) == name
+
+
+def test_out_dtype_table(L):
+    table = {(F32, SUM): F32, (F16, SUM): F32, (BF16, SUM): F32, (F16, MAX): F16, (BF16, MIN): BF16,
+             (F16, PROD): F32, (F64, PROD): F64, (I32, SUM): I64, (I32, MAX): I32, (I32, PROD): I32,
+             (U32, SUM): U32, (U32, XOR): U32, (I64, SUM): I64}
+    for (d, o), want in table.items():
+        assert pr.pr_out_dtype(d, o) == want
+
+
+def _msg():
+    return pr.pr_last_error_message()
+
+
+@pytest.mark.parametrize("args,status,needle", [
+    ((FAKE, -1, F32, SUM, FAKE, None), INVALID, "n must be"),
+    ((None, 10, F32, SUM, FAKE, None), INVALID, "x is NULL"),
+    ((FAKE, 10, F32, SUM, None, None), INVALID, "out is NULL"),
+    ((FAKE, 10, F32, AND, FAKE, None), UNSUPPORTED, "bitwise"),
+    ((FAKE, 10, BF16, XOR, FAKE, None), UNSUPPORTED, "bitwise"),
+    ((FAKE, 10, 99, SUM, FAKE, None), INVALID, "dtype"),
+    ((FAKE, 10, F32, 42, FAKE, None), INVALID, "op"),
+    ((FAKE + 2, 10, F32, SUM, FAKE, None), INVALID, "aligned"),
+    ((FAKE + 4, 10, F64, MAX, FAKE, None), INVALID, "aligned"),
+])
+def test_reduce_rejects(L, args, status, needle):
+    assert pr.pr_reduce(*args) == status
+    assert needle in _msg()
+
+
+def test_reduce_ex_precision_and_out_dtype_rules(L):
+    assert pr.pr_reduce_ex(FAKE, 10, I32, SUM, COMP, I64, FAKE, None) == UNSUPPORTED
+    assert pr.pr_reduce_ex(FAKE, 10, F32, MAX, F64C, F32, FAKE, None) == UNSUPPORTED
+    assert pr.pr_reduce_ex(FAKE, 10, F64, SUM, COMP, F64, FAKE, None) == UNSUPPORTED
+    assert pr.pr_reduce_ex(FAKE, 10, F32, SUM, PLAIN, F64, FAKE, None) == UNSUPPORTED
+    assert pr.pr_reduce_ex(FAKE, 10, F32, SUM, 7, F32, FAKE, None) == INVALID
+
+
+def test_segmented_rejects(L):
+    assert pr.pr_segmented_reduce(FAKE, FAKE, -1, F32, SUM, FAKE, None) == INVALID
+    assert pr.pr_segmented_reduce(FAKE, None, 4, F32, SUM, FAKE, None) == INVALID
+    assert pr.pr_segmented_reduce(None, FAKE, 4, F32, SUM, FAKE, None) == INVALID
+    assert pr.pr_segmented_reduce(FAKE, FAKE, 4, F32, SUM, None, None) == INVALID
+    assert pr.pr_segmented_reduce_aux(FAKE, FAKE, 4, F32, SUM, PLAIN, FAKE, FAKE, None, None) == UNSUPPORTED
+    assert pr.pr_segmented_reduce_aux(FAKE, FAKE, 4, F32, MAX, PLAIN, FAKE, None, FAKE, None) == UNSUPPORTED
+    assert pr.pr_segmented_reduce_aux(FAKE, FAKE, 4, F16, PROD, PLAIN, FAKE, None, FAKE, None) == UNSUPPORTED
+    assert pr.pr_segmented_reduce(FAKE, FAKE, 4, F32, OR, FAKE, None) == UNSUPPORTED
+    # zero segments: nothing to do, nothing enqueued
+    assert pr.pr_segmented_reduce(None, None, 0, F32, SUM, None, None) == OK
+
+
+def test_rows_and_backward_reject(L):
+    assert pr.pr_reduce_rows(FAKE, -1, 4, F32, SUM, PLAIN, FAKE, None, None, None) == INVALID
+    assert pr.pr_reduce_rows(FAKE, 2 ** 40, 2 ** 40, F32, SUM, PLAIN, FAKE, None, None, None) == INVALID
+    assert pr.pr_reduce_rows(None, 4, 4, F32, SUM, PLAIN, FAKE, None, None, None) == INVALID
+    assert pr.pr_reduce_backward(SUM, I32, FAKE, 4, 4, FAKE, None, None, FAKE, None) == UNSUPPORTED
+    assert pr.pr_reduce_backward(AND, F32, FAKE, 4, 4, FAKE, None, None, FAKE, None) == UNSUPPORTED
+    assert pr.pr_reduce_backward(MAX, F32, None, 4, 4, FAKE, None, None, FAKE, None) == INVALID
+    assert pr.pr_reduce_backward(PROD, F32, None, 4, 4, FAKE, None, FAKE, FAKE, None) == INVALID
+    assert pr.pr_reduce_backward(SUM, F32, None, 0, 4, None, None, None, None, None) == OK
+
+
+def test_host_path_rejects(L):
+    assert pr.pr_reduce_host(None, 5, F32, SUM, FAKE, None) == INVALID
+    assert pr.pr_reduce_host(FAKE, 5, F32, SUM, None, None) == INVALID
+    assert pr.pr_reduce_host(FAKE, 5, F32, XOR, FAKE, None) == UNSUPPORTED
+
+
+def test_config_roundtrip_and_validation(L):
+    c = pr.pr_config(512, 2, 4, 16)
+    assert pr.pr_set_config(0, F32, SUM, PLAIN, 1 << 20, ctypes.byref(c)) == OK
+    got = pr.pr_config()
+    assert pr.pr_get_config(0, F32, SUM, PLAIN, (1 << 20) + 5, ctypes.byref(got)) == OK
+    assert got.as_dict() == c.as_dict()
+    for bad in ((100, 2, 4, 16), (512, 0, 4, 16), (512, 2, 3, 16), (512, 2, 4, 8), (2048, 1, 4, 16)):
+        assert pr.pr_set_config(0, F32, SUM, PLAIN, 1, ctypes.byref(pr.pr_config(*bad))) == INVALID
+
+
+def test_valid_call_without_a_gpu_fails_loudly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    # validation passes, the CUDA runtime then reports the missing device
+    assert pr.pr_reduce(FAKE, 10, F32, SUM, FAKE, None) == CUDA
+    with pytest.raises(pr.PrError):
+        pr.check(pr.pr_reduce(FAKE, 10, F32, SUM, FAKE, None))
