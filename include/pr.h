@@ -186,6 +186,33 @@ pr_status pr_reduce_host(const void* host_x, int64_t n, pr_dtype dtype, pr_op op
                          void* host_out, pr_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* Plain reduction without any library allocation                          */
+/* ---------------------------------------------------------------------- */
+
+/* out[0] = x[0] (x) ... (x) x[n-1], like pr_reduce (PLAIN precision), for
+ * callers that cannot allocate device memory when they reduce -- code inside
+ * a memory pool or arena that owns every allocation, allocation-free
+ * real-time paths, or hosts that forbid pr_reduce's implicit first-use
+ * workspace allocation.  The paper has no counterpart: this is a deployment
+ * variant of the same kernel.  Its scratch (1024 block partials of 64 bytes
+ * and a ticket counter, 64.25 KiB) is a static array in device memory that
+ * every GPU loading libpr.so holds until the process exits; the entry point
+ * calls no cudaMalloc / cudaFree.  The caller passes x and out as for
+ * pr_reduce.
+ *   - A launch needing more than 1024 block partials is rejected with
+ *     PR_ERR_UNSUPPORTED (GB300 uses 304).
+ *   - All calls share the one array: calls whose kernels overlap on the GPU
+ *     (e.g. on different streams) race; serialise them.
+ *   - The first call on a device sets up the array's device address on that
+ *     device (so make it before any stream capture); the ticket that must
+ *     start at zero is cleared on `stream` before every launch.
+ *   - Launch shape is fixed (512 threads, up to 2 blocks per SM, 2 x 32-byte
+ *     vectors per thread), so float SUM/PROD bits may differ from pr_reduce's
+ *     tuned launch within the same error bounds. */
+pr_status pr_reduce_noalloc(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* out,
+                            pr_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Set-up, status and tuning                                                */
 /* ---------------------------------------------------------------------- */
 

@@ -35,7 +35,7 @@ const KernelEntry* reg_find(const KernelKey& k) {
     return it == table().end() ? nullptr : &it->second;
 }
 
-static void ensure_registered() {
+void ensure_registered() {
     static std::once_flag once;
     std::call_once(once, [] {
         register_f32();
@@ -56,7 +56,7 @@ static void ensure_registered() {
 
 static thread_local std::string g_msg;
 
-static pr_status fail(pr_status s, const char* fmt, ...) {
+pr_status fail(pr_status s, const char* fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);

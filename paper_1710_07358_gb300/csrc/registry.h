@@ -47,4 +47,7 @@ void register_u32();
 void register_i64();
 void register_backward();
 
+// Registers every family above exactly once (thread-safe).
+void ensure_registered();
+
 }  // namespace pr

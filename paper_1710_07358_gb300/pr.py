@@ -55,6 +55,7 @@ _SIGS = {
     "pr_reduce_rows": [_P, _I64, _I64, _I, _I, _I, _P, _P, _P, _P],
     "pr_reduce_backward": [_I, _I, _P, _I64, _I64, _P, _P, _P, _P, _P],
     "pr_reduce_host": [_P, _I64, _I, _I, _P, _P],
+    "pr_reduce_noalloc": [_P, _I64, _I, _I, _P, _P],
     "pr_prepare": [_P],
     "pr_last_device_error": [_P, ctypes.POINTER(_I32)],
     "pr_get_config": [_I, _I, _I, _I, _I64, ctypes.POINTER(pr_config)],
@@ -133,6 +134,10 @@ def pr_reduce_backward(op, dtype, x, rows, cols, grad_out, argidx, aux, grad_in,
 
 def pr_reduce_host(host_x, n, dtype, op, host_out, stream):
     return lib().pr_reduce_host(host_x, n, dtype, op, host_out, stream)
+
+
+def pr_reduce_noalloc(x, n, dtype, op, out, stream):
+    return lib().pr_reduce_noalloc(x, n, dtype, op, out, stream)
 
 
 def pr_prepare(stream):
