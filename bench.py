@@ -165,7 +165,10 @@ def cpu_oracle_sum(x):
 # Secondary forms (all on the same GPU, same run)
 # --------------------------------------------------------------------------
 
-def forms(steps, warmup, peak):
+FORM_GROUPS = ("plain", "precision", "illcond", "segmented", "fwdbwd")
+
+
+def forms(steps, warmup, peak, only=None, tune=True):
     import numpy as np
     import torch
     from paper_1710_07358_gb300 import pr, synth
@@ -182,30 +185,56 @@ def forms(steps, warmup, peak):
         res[name] = {"GB/s": round(gbs(nb, per), 1), "frac": round(gbs(nb, per) / peak, 4),
                      "us": round(per * 1e3, 2)}
 
+    want = set(only or FORM_GROUPS)
     n = N_HEAD
     g.manual_seed(synth.config_seed(1))
-    f32 = torch.rand(n, generator=g, device=dev) * 2 - 1
-    for op in ("sum", "max", "min"):
-        plain("f32_%s" % op, f32, op)
-    i32 = torch.randint(-(1 << 20), 1 << 20, (n,), generator=g, device=dev, dtype=torch.int32)
-    for op in ("sum", "max", "min"):
-        plain("i32_%s" % op, i32, op)
-    del i32
-    u32 = torch.randint(-(1 << 31), (1 << 31) - 1, (n,), generator=g, device=dev, dtype=torch.int32).view(torch.uint32)
-    for op in ("and", "or", "xor"):
-        plain("u32_%s" % op, u32, op)
-    del u32
-    f64 = torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 0.002 + 0.999
-    plain("f64_prod", f64, "prod")
-    del f64
-    for dt, name in ((torch.bfloat16, "bf16"), (torch.float16, "f16")):
-        h = torch.randn(n, generator=g, device=dev).to(dt)
-        plain("%s_sum" % name, h, "sum")
-        plain("%s_sum_compensated" % name, h, "sum", precision="compensated")
-        del h
-    plain("f32_sum_compensated", f32, "sum", precision="compensated")
-    plain("f32_sum_fp64_combine", f32, "sum", precision="fp64_combine")
-    del f32
+    if "plain" in want or "precision" in want:
+        f32 = torch.rand(n, generator=g, device=dev) * 2 - 1
+    if "plain" in want:
+        for op in ("sum", "max", "min"):
+            plain("f32_%s" % op, f32, op)
+        i32 = torch.randint(-(1 << 20), 1 << 20, (n,), generator=g, device=dev, dtype=torch.int32)
+        for op in ("sum", "max", "min"):
+            plain("i32_%s" % op, i32, op)
+        del i32
+        u32 = torch.randint(-(1 << 31), (1 << 31) - 1, (n,), generator=g, device=dev,
+                            dtype=torch.int32).view(torch.uint32)
+        for op in ("and", "or", "xor"):
+            plain("u32_%s" % op, u32, op)
+        del u32
+        f64 = torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 0.002 + 0.999
+        plain("f64_prod", f64, "prod")
+        del f64
+    if "precision" in want:
+        for dt, name in ((torch.bfloat16, "bf16"), (torch.float16, "f16")):
+            h = torch.randn(n, generator=g, device=dev).to(dt)
+            plain("%s_sum" % name, h, "sum")
+            plain("%s_sum_compensated" % name, h, "sum", precision="compensated")
+            del h
+        plain("f32_sum_compensated", f32, "sum", precision="compensated")
+        plain("f32_sum_fp64_combine", f32, "sum", precision="fp64_combine")
+    if "plain" in want or "precision" in want:
+        del f32
+    if "illcond" in want:
+        ill(res, k, warmup, peak, st)
+    if "segmented" in want:
+        segmented(res, k, warmup, peak, tune)
+    if "fwdbwd" in want:
+        fwdbwd(res, k, warmup, peak, st, g)
+    return res
+
+
+def ill(res, k, warmup, peak, st):
+    import numpy as np
+    import torch
+    from paper_1710_07358_gb300 import pr, synth
+    dev = torch.device("cuda")
+
+    def plain(name, t, op, **kw):
+        nb = t.numel() * t.element_size()
+        _, per = time_launches(lambda: pr.reduce(t, op, **kw), k, warmup, st)
+        res[name] = {"GB/s": round(gbs(nb, per), 1), "frac": round(gbs(nb, per) / peak, 4),
+                     "us": round(per * 1e3, 2)}
 
     # precision: ill-conditioned fp32 set, error against the exact sum (known by construction)
     x, n_big, exact = synth.ill_conditioned_f32(1 << 26, synth.config_seed(2))
@@ -219,13 +248,19 @@ def forms(steps, warmup, peak):
     res["illcond_errors"] = {"n": 1 << 26, "exact": exact, "kappa": abs_sum / exact, **errs}
     del xt
 
+
+def segmented(res, k, warmup, peak, tune=True):
+    import torch
+    from paper_1710_07358_gb300 import pr, synth
+    dev = torch.device("cuda")
     # segmented: 4096 log-uniform segments, autotuned, replayed from a CUDA graph
     vals, off = synth.segmented_workload(4096, synth.config_seed(3))
     xv = torch.from_numpy(vals).to(dev)
     ov = torch.from_numpy(off).to(dev)
     seg_bytes = 4 * vals.size + 8 * off.size + 4 * 4096
     for op in ("sum", "max"):
-        cfg = pr.autotune("segmented", xv, op, offsets=ov)
+        cfg = pr.autotune("segmented", xv, op, offsets=ov) if tune else \
+            pr.get_config("segmented", "f32", op, "plain", 4096)
         out = torch.empty(4096, dtype=torch.float32, device=dev)
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
@@ -243,6 +278,11 @@ def forms(steps, warmup, peak):
                                     "graph": True}
     del xv, ov
 
+
+def fwdbwd(res, k, warmup, peak, st, g):
+    import torch
+    from paper_1710_07358_gb300 import pr
+    dev = torch.device("cuda")
     # differentiation: [64, 2^20] fp32, forward + backward
     rows, cols = 64, 1 << 20
     xr = torch.randn(rows, cols, generator=g, device=dev)
@@ -277,7 +317,6 @@ def forms(steps, warmup, peak):
                                   "fwd_bwd_GB/s": round(gbs(2 * mat, pf + pb), 1),
                                   "frac": round(gbs(2 * mat, pf + pb) / peak, 4),
                                   "us": round((pf + pb) * 1e3, 2)}
-    return res
 
 
 # --------------------------------------------------------------------------
@@ -290,6 +329,40 @@ def smi_index(local):
     if local < len(ids) and ids[local].isdigit():
         return int(ids[local])
     return local
+
+
+def gpu_local_cpus(index):
+    """CPUs of the NUMA node the GPU is attached to (sysfs), or None."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().lower()
+        dom, rest = out.split(":", 1)
+        path = "/sys/bus/pci/devices/%04x:%s/local_cpulist" % (int(dom, 16) & 0xffff, rest)
+        with open(path) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return cpus & os.sched_getaffinity(0) or None
+    except Exception:
+        return None
+
+
+def pinned_near_gpu(x_host, index):
+    """Pinned host copy of x_host placed on the GPU's NUMA node: the pages are
+    allocated and first touched by this process bound to that node's CPUs."""
+    import torch
+    cpus = gpu_local_cpus(index)
+    old = os.sched_getaffinity(0)
+    try:
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        t = torch.empty(x_host.shape, dtype=torch.from_numpy(x_host[:1]).dtype).pin_memory()
+        t.copy_(torch.from_numpy(x_host))
+    finally:
+        os.sched_setaffinity(0, old)
+    return t, sorted(cpus) if cpus else None
 
 
 def dist_env():
@@ -383,7 +456,7 @@ def run_ours(args):
     # end to end: pinned host buffer through the C ABI
     e2e = None
     if not args.no_e2e:
-        pinned = torch.from_numpy(x_host).pin_memory()
+        pinned, near = pinned_near_gpu(x_host, smi_index(dev.index))
         ke = max(3, min(args.steps, 10))
         pr.reduce_host(pinned, "sum")
         torch.cuda.synchronize()
@@ -399,7 +472,9 @@ def run_ours(args):
             e2e_s = tt.item()
         e2e_s /= ke
         e2e = {"value": round(gbs(nbytes * world, e2e_s * 1e3), 1), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": 4, "steps": ke}
+               "d2h_bytes_per_step": 4, "steps": ke,
+               "host_buffer": "pinned, on the GPU's NUMA node (cpus %s)" % (
+                   "%d-%d" % (near[0], near[-1]) if near else "unknown")}
 
     achieved = gbs(nbytes, per_launch)
     cfg = pr.get_config("reduce", "f32", "sum", "plain", N_HEAD)
@@ -429,7 +504,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_forms:
         del x
         torch.cuda.empty_cache()
-        line["forms"] = forms(args.steps, args.warmup, peak)
+        line["forms"] = forms(args.steps, args.warmup, peak, tune=not args.no_tune)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -446,6 +521,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="segmented form: use the shipped tuning table instead of re-running the autotuner")
+    ap.add_argument("--forms-only", default=None,
+                    help="comma list of %s: run only these secondary forms (profiling)" % ",".join(FORM_GROUPS))
     ap.add_argument("--n-log2", type=int, default=28,
                     help="headline size 2^k (28 is the measured workload; smaller only for profiling)")
     args = ap.parse_args()
@@ -457,7 +536,18 @@ def main():
         WORKLOAD = "plain fp32 sum, n=2^%d uniform[-1,1) (profiling case, not the measured workload)" % args.n_log2
     if args.impl == "reference":
         return run_reference(args)
+    if args.forms_only:
+        return run_forms_only(args)
     return run_ours(args)
+
+
+def run_forms_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    peak, _ = measured_peaks()
+    only = [f.strip() for f in args.forms_only.split(",") if f.strip()]
+    print(json.dumps({"forms": forms(args.steps, args.warmup, peak, only, tune=not args.no_tune)}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -158,6 +158,8 @@ static pr_status get_ws(cudaStream_t st, Workspace* out) {
     unsigned* u = reinterpret_cast<unsigned*>(b + (size_t)3 * gmax * kSlot);
     ws.seg_cnt = u;
     ws.counter = u + gmax;
+    ws.chunk_ctr = u + gmax + 1;
+    ws.blk_done = u + gmax + 2;
     ws.err = reinterpret_cast<int*>(u + gmax + 32);
     ws.gmax = gmax;
     g_ws[key] = WsRec{ws, base, bytes};
@@ -184,12 +186,14 @@ static std::map<CfgKey, pr_config> g_tuned;
 static pr_config default_cfg(int kind, int dtype, int op, int prec) {
     (void)dtype; (void)op; (void)prec;
     if (kind == PR_KIND_BACKWARD) return pr_config{512, 4, 4, 16};
-    if (kind == PR_KIND_SEGMENTED) return pr_config{256, 4, 4, 32};
+    if (kind == PR_KIND_SEGMENTED) return pr_config{256, 2, 4, 32};
     return pr_config{512, 2, 2, 32};
 }
 
-static bool cfg_valid(const pr_config& c) {
-    if (c.block < 64 || c.block > 1024 || c.block % 32) return false;
+// The segmented kernel is built for blocks of at most 512 threads (it keeps
+// two tiles of vectors per thread in registers).
+static bool cfg_valid(const pr_config& c, int kind = PR_KIND_REDUCE) {
+    if (c.block < 64 || c.block > (kind == PR_KIND_SEGMENTED ? 512 : 1024) || c.block % 32) return false;
     if (c.blocks_per_sm < 1 || c.blocks_per_sm > 32) return false;
     if (c.unroll != 2 && c.unroll != 4) return false;
     return c.vec_bytes == 16 || c.vec_bytes == 32;
@@ -260,6 +264,23 @@ static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int pre
     return PR_OK;
 }
 
+// Segmented work split, measured on GB300: every chunk switch or segment
+// boundary costs a block a combine (~3 us with its loads drained), so with few
+// segments per block one static chunk per block is fastest (64 rows of 2^20:
+// 49 us vs 58 us with 4 chunks), while many uneven segments want several
+// chunks claimed dynamically (4096 log-uniform segments: 203 us vs 220 us).
+static void seg_split(int64_t nseg, int grid, int gmax, int* chunks_per_block, int* dynamic) {
+    if (nseg > 2 * (int64_t)grid) {
+        int c = 8;
+        while (c > 1 && (int64_t)c * grid > gmax) c >>= 1;
+        *chunks_per_block = c;
+        *dynamic = 1;
+    } else {
+        *chunks_per_block = 1;
+        *dynamic = 0;
+    }
+}
+
 static pr_status run_segmented(const void* x, const int64_t* off, int64_t cols, int64_t nseg, int dtype, int op,
                                int prec, int aux, void* out, int64_t* argidx, pr_prod_aux* paux, cudaStream_t st,
                                const pr_config& c) {
@@ -278,7 +299,9 @@ static pr_status run_segmented(const void* x, const int64_t* off, int64_t cols, 
     if (s != PR_OK) return s;
     const int es = elem_size(dtype);
     const int64_t shift = (int64_t)(reinterpret_cast<uintptr_t>(x) % (uintptr_t)c.vec_bytes) / es;
-    SegArgs a{x, off, cols, nseg, shift, out, argidx, paux, 0, ws};
+    int cpb = 1, dyn = 0;
+    seg_split(nseg, grid, ws.gmax, &cpb, &dyn);
+    SegArgs a{x, off, cols, nseg, shift, out, argidx, paux, 0, cpb, dyn, ws};
     cudaError_t err = reinterpret_cast<SegLaunch>(e->launch)(a, grid, c.block, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "segmented launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -578,8 +601,8 @@ pr_status pr_get_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision pre
 pr_status pr_set_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision precision, int64_t n,
                         const pr_config* cfg) {
     g_msg.clear();
-    if (!cfg || !cfg_valid(*cfg)) return fail(PR_ERR_INVALID, "invalid configuration");
     if (kind < PR_KIND_REDUCE || kind > PR_KIND_BACKWARD) return fail(PR_ERR_INVALID, "unknown kind");
+    if (!cfg || !cfg_valid(*cfg, kind)) return fail(PR_ERR_INVALID, "invalid configuration for kind %d", kind);
     std::lock_guard<std::mutex> lk(g_mu);
     g_tuned[CfgKey{kind, dtype, op, precision, bucket_of(n)}] = *cfg;
     return PR_OK;
@@ -610,11 +633,11 @@ pr_status pr_autotune(pr_kind kind, const void* x, int64_t n, const int64_t* off
     const bool f64 = false;
     float best_ms = 1e30f;
     pr_config best_c = default_cfg(kind, dtype, op, precision);
-    const int blocks[] = {256, 512, 1024};
+    const int blocks[] = {128, 256, 512, 1024};
     const int bpss[] = {1, 2, 4, 8};
     for (int blk : blocks)
         for (int bps : bpss) {
-            if (blk * bps > 2048) continue;
+            if (blk * bps > 2048 || !cfg_valid(pr_config{blk, bps, 2, 16}, kind)) continue;
             for (int u : kUnrolls)
                 for (int vb : kVecBytes) {
                     const pr_config c{blk, bps, u, vb};
@@ -705,7 +728,7 @@ pr_status pr_tune_load(const char* path) {
                    "{\"kind\": %d, \"dtype\": %d, \"op\": %d, \"precision\": %d, \"bucket\": %d, \"block\": %d, "
                    "\"blocks_per_sm\": %d, \"unroll\": %d, \"vec_bytes\": %d}",
                    &kind, &dtype, &op, &prec, &bucket, &c.block, &c.blocks_per_sm, &c.unroll, &c.vec_bytes) != 9 ||
-            !cfg_valid(c))
+            !cfg_valid(c, kind))
             return fail(PR_ERR_INVALID, "malformed tuning entry at byte %zu", pos);
         fresh[CfgKey{kind, dtype, op, prec, bucket}] = c;
         loaded++;

@@ -15,18 +15,22 @@
 //
 // k_segmented  many reductions (segments of a CSR offsets array, or equal rows)
 //   in one launch.  The element range [offsets[0], offsets[nseg]) is cut into
-//   tiles of blockDim*U*VB bytes and every block owns a contiguous run of
-//   tiles.  Inside a tile that lies in one segment the block streams exactly
-//   like k_reduce; a tile containing segment boundaries emits the finished
+//   tiles of blockDim*U*VB bytes, and runs of tiles form chunks (about four
+//   per block) that blocks claim dynamically from an atomic counter, so that
+//   blocks delayed by many segment boundaries do not hold up the launch.
+//   Inside a tile that lies in one segment the block streams exactly like
+//   k_reduce; a tile containing segment boundaries emits the finished
 //   segment, reduces the segments that lie wholly inside the tile (short ones
 //   one per warp, long ones with the whole block) and starts the next one.
-//   A segment that crosses block boundaries leaves one partial per block it
-//   touches (its first block's "tail" slot, later blocks' "head" slots); the
-//   last of those blocks to arrive (per-segment ticket) combines them in block
-//   order.  Results are deterministic for a fixed launch configuration.
+//   A segment that crosses chunk boundaries leaves one partial per chunk it
+//   touches (its first chunk's "tail" slot, later chunks' "head" slots); the
+//   last of those chunks to finish (per-segment ticket) combines them in chunk
+//   order.  Partials are indexed by chunk, not by block, so results are
+//   deterministic for a fixed launch configuration whatever the claim order.
 //
 // k_combine_parts  one block combining an array of partials in order.
 #pragma once
+#include <type_traits>
 #include "traits.cuh"
 
 namespace pr {
@@ -41,6 +45,8 @@ struct Workspace {
     char* tail;          // gmax slots (k_segmented: last-segment partial of a block)
     unsigned* seg_cnt;   // gmax tickets (k_segmented), zero between launches
     unsigned* counter;   // 1 ticket (k_reduce), zero between launches
+    unsigned* chunk_ctr; // next chunk to claim (k_segmented), zero between launches
+    unsigned* blk_done;  // blocks finished (k_segmented), zero between launches
     int* err;            // device error word
     int gmax;
 };
@@ -65,6 +71,8 @@ struct SegArgs {
     int64_t* argidx;
     pr_prod_aux* aux;
     int out_f64;
+    int chunks_per_block;  // chunks (contiguous tile runs) per block
+    int dynamic_chunks;    // 1: blocks claim chunks from an atomic counter; 0: chunk c -> block c mod grid
     Workspace ws;
 };
 
@@ -80,6 +88,34 @@ struct BwdArgs {
     int op;
 };
 
+
+// The value that crosses blocks.  By default a block's partial crosses as the
+// trait's Part; a trait may declare a wider GridPart (with to_grid, grid_init,
+// grid_combine, grid_store) used only for combining block partials -- the
+// compensated sum keeps fp32 pairs inside a block and combines blocks in fp64.
+template <class T, class = void>
+struct GridR {
+    using Part = typename T::Part;
+    __device__ __forceinline__ static Part up(const typename T::Part& p) { return p; }
+    __device__ __forceinline__ static Part part_init() { return T::part_init(); }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return T::combine(a, b); }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return T::warp_reduce(p); }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) { T::store(out, i, p, f64); }
+    __device__ __forceinline__ static void store_aux(int64_t* ai, pr_prod_aux* ax, int64_t i, const Part& p, int64_t sb) {
+        T::store_aux(ai, ax, i, p, sb);
+    }
+};
+
+template <class T>
+struct GridR<T, std::void_t<typename T::GridPart>> {
+    using Part = typename T::GridPart;
+    __device__ __forceinline__ static Part up(const typename T::Part& p) { return T::to_grid(p); }
+    __device__ __forceinline__ static Part part_init() { return T::grid_init(); }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return T::grid_combine(a, b); }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<GridR>(p); }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) { T::grid_store(out, i, p, f64); }
+    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
+};
 
 template <class T>
 __device__ __forceinline__ typename T::Part* slot(char* base, int64_t i) {
@@ -138,11 +174,13 @@ __global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a) {
     if (tid < head) T::add(acc[0], Ld::one(x, tid), tid);
     for (int64_t j = head + nvec * VE + tid; j < a.n; j += nth) T::add(acc[0], Ld::one(x, j), j);
 
-    Part p = block_combine<T>(fold<T, U>(acc));
+    using GR = GridR<T>;
+    using G = typename GR::Part;
+    const Part p = block_combine<T>(fold<T, U>(acc));
 
     __shared__ unsigned s_last;
     if (threadIdx.x == 0) {
-        *slot<T>(a.ws.partials, blockIdx.x) = p;
+        *slot<GR>(a.ws.partials, blockIdx.x) = GR::up(p);
         __threadfence();
         const unsigned ticket = atomicAdd(a.ws.counter, 1u);
         s_last = (ticket == gridDim.x - 1);
@@ -150,12 +188,12 @@ __global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    Part q = T::part_init();
-    for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) q = T::combine(q, ld_cg_any(slot<T>(a.ws.partials, j)));
-    q = block_combine<T>(q);
+    G q = GR::part_init();
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) q = GR::combine(q, ld_cg_any(slot<GR>(a.ws.partials, j)));
+    q = block_combine<GR>(q);
     if (threadIdx.x == 0) {
-        if (a.part_out) *static_cast<Part*>(a.part_out) = q;
-        else T::store(a.out, 0, q, a.out_f64 != 0);
+        if (a.part_out) *static_cast<G*>(a.part_out) = q;
+        else GR::store(a.out, 0, q, a.out_f64 != 0);
         *a.ws.counter = 0u;
     }
 }
@@ -163,12 +201,13 @@ __global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a) {
 // One block: out = parts[0] (x) parts[1] (x) ... in index order (slot stride kSlot).
 template <class T>
 __global__ void __launch_bounds__(256) k_combine_parts(const char* parts, int count, void* out, int out_f64) {
-    using Part = typename T::Part;
-    Part q = T::part_init();
+    using GR = GridR<T>;
+    using G = typename GR::Part;
+    G q = GR::part_init();
     for (int j = threadIdx.x; j < count; j += blockDim.x)
-        q = T::combine(q, *reinterpret_cast<const Part*>(parts + (int64_t)j * kSlot));
-    q = block_combine<T>(q);
-    if (threadIdx.x == 0) T::store(out, 0, q, out_f64 != 0);
+        q = GR::combine(q, *reinterpret_cast<const G*>(parts + (int64_t)j * kSlot));
+    q = block_combine<GR>(q);
+    if (threadIdx.x == 0) GR::store(out, 0, q, out_f64 != 0);
 }
 
 // ------------------------------------------------------------------------
@@ -186,19 +225,34 @@ struct Segs {
         return b < P0 ? P0 : (b > P1 ? P1 : b);
     }
     __device__ __forceinline__ int64_t end(int64_t s) const { return begin(s + 1); }
-    // largest s in [lo, nseg) with begin(s) <= p   (requires begin(lo) <= p)
-    __device__ int64_t find(int64_t lo, int64_t p) const {
+    // Largest s in [lo, nseg) with begin(s) <= p (requires begin(lo) <= p),
+    // found by one warp (all 32 lanes call; every lane gets the answer).
+    // begin() is non-decreasing, so {s : begin(s) <= p} is a prefix of
+    // [lo, nseg): one coalesced probe of the next 32 segments settles the
+    // common case (the answer is near lo), else a 32-ary search narrows the
+    // interval 32-fold per round.
+    __device__ int64_t find(int64_t lo, int64_t p, int lane) const {
         if (!off) {
             int64_t s = p / cols;
             s = s < lo ? lo : s;
             return s > nseg - 1 ? nseg - 1 : s;
         }
-        int64_t l = lo, r = nseg - 1;
-        while (l < r) {
-            const int64_t m = (l + r + 1) >> 1;
-            if (begin(m) <= p) l = m; else r = m - 1;
+        int64_t hi = nseg - 1;
+        {
+            const int64_t q = lo + 1 + lane;
+            const unsigned m = __ballot_sync(0xffffffffu, q <= hi && begin(q) <= p);
+            if (m != 0xffffffffu) return lo + __popc(m);
+            lo += 32;
         }
-        return l;
+        while (lo < hi) {
+            const int64_t step = (hi - lo + 32) / 32;
+            const int64_t q = lo + (int64_t)lane * step;
+            const unsigned m = __ballot_sync(0xffffffffu, q <= hi && begin(q) <= p);
+            const int last = 31 - __clz(m);
+            lo = lo + (int64_t)last * step;
+            hi = lo + step - 1 < hi ? lo + step - 1 : hi;
+        }
+        return lo;
     }
 };
 
@@ -236,8 +290,28 @@ struct SegCtx {
     }
 };
 
+// Same as SegCtx::masked, from vectors already loaded for an interior tile.
 template <class T, int U, int VB>
-__global__ void __launch_bounds__(1024) k_segmented(SegArgs a) {
+__device__ __forceinline__ void masked_words(typename T::Acc (&acc)[U], const Words<VB> (&w)[U], int64_t tlo,
+                                             int64_t lo, int64_t hi) {
+    using Ld = typename T::Ld;
+    using E = typename Ld::E;
+    constexpr int VE = VB / Ld::ES;
+    if (lo >= hi) return;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int64_t vp = tlo + ((int64_t)u * blockDim.x + threadIdx.x) * VE;
+        if (vp + VE <= lo || vp >= hi) continue;
+        E e[VE];
+        Ld::template dec<VB>(w[u], e);
+#pragma unroll
+        for (int k = 0; k < VE; k++)
+            if (vp + k >= lo && vp + k < hi) T::add(acc[u], e[k], vp + k);
+    }
+}
+
+template <class T, int U, int VB>
+__global__ void __launch_bounds__(512) k_segmented(SegArgs a) {
     using Ld = typename T::Ld;
     using In = typename Ld::In;
     using E = typename Ld::E;
@@ -271,130 +345,192 @@ __global__ void __launch_bounds__(1024) k_segmented(SegArgs a) {
     const int64_t shift = a.shift;
     const int64_t J0 = ((P0 + shift) / VE) * VE;  // first VB boundary at or before P0
     const int64_t ntiles = (P1 + shift - J0 + TILE - 1) / TILE;
-    const int64_t K = (ntiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * K;
-    const int64_t t1 = t0 + K < ntiles ? t0 + K : ntiles;
-    if (t0 >= t1) return;
+    // chunks: a few per block, at most one slot pair per chunk
+    int64_t nchunk = (int64_t)a.chunks_per_block * gridDim.x;
+    nchunk = nchunk < a.ws.gmax ? nchunk : a.ws.gmax;
+    nchunk = nchunk < ntiles ? nchunk : ntiles;
+    const int64_t K = (ntiles + nchunk - 1) / nchunk;  // tiles per chunk
+    nchunk = (ntiles + K - 1) / K;                      // chunks that hold tiles
     const int64_t CB = K * TILE;
-    const int64_t blk_lo = (J0 + t0 * TILE - shift) > P0 ? (J0 + t0 * TILE - shift) : P0;
-    const int64_t blk_hi = (J0 + t1 * TILE - shift) < P1 ? (J0 + t1 * TILE - shift) : P1;
 
     SegCtx<T, U, VB> ctx{x, sg, P0, P1};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = B >> 5;
 
     __shared__ int64_t s_i64;
     __shared__ int s_fin;
+    __shared__ unsigned s_chunk;
+    using GR = GridR<T>;
+    using G = typename GR::Part;
 
-    // Finish this block's piece of segment s (all threads call).
-    auto emit = [&](int64_t s, Acc (&acc)[U]) {
-        Part p = block_combine<T>(fold<T, U>(acc));
+    for (int64_t iter = 0;; iter++) {
+        int64_t c;
+        if (a.dynamic_chunks) {
+            __syncthreads();  // s_chunk / s_i64 of the previous chunk are consumed
+            if (threadIdx.x == 0) s_chunk = atomicAdd(a.ws.chunk_ctr, 1u);
+            __syncthreads();
+            c = s_chunk;
+        } else {
+            c = blockIdx.x + iter * gridDim.x;
+        }
+        if (c >= nchunk) break;
+        const int64_t t0 = c * K;
+        const int64_t t1 = t0 + K < ntiles ? t0 + K : ntiles;
+        const int64_t blk_lo = (J0 + t0 * TILE - shift) > P0 ? (J0 + t0 * TILE - shift) : P0;
+        const int64_t blk_hi = (J0 + t1 * TILE - shift) < P1 ? (J0 + t1 * TILE - shift) : P1;
+
+        // Finish this chunk's piece of segment s (all threads call).
+        auto emit = [&](int64_t s, Acc (&acc)[U]) {
+            const Part p = block_combine<T>(fold<T, U>(acc));
+#pragma unroll
+            for (int u = 0; u < U; u++) acc[u] = T::init();
+            const int64_t sb = sg.begin(s), se = sg.end(s);
+            if (sb >= blk_lo && se <= blk_hi) {
+                if (threadIdx.x == 0) {
+                    const G g = GR::up(p);
+                    GR::store(a.out, s, g, f64);
+                    GR::store_aux(a.argidx, a.aux, s, g, sb);
+                }
+                return;
+            }
+            const int64_t ba = (sb + shift - J0) / CB, bb = (se - 1 + shift - J0) / CB;
+            if (threadIdx.x == 0) {
+                *slot<GR>(sb < blk_lo ? a.ws.head : a.ws.tail, c) = GR::up(p);
+                __threadfence();
+                const unsigned old = atomicAdd(a.ws.seg_cnt + ba, 1u);
+                s_fin = (old == (unsigned)(bb - ba));
+            }
+            __syncthreads();
+            if (s_fin && warp == 0) {
+                __threadfence();
+                G q = GR::part_init();
+                for (int64_t k = lane; k <= bb - ba; k += 32)
+                    q = GR::combine(q, ld_cg_any(k == 0 ? slot<GR>(a.ws.tail, ba) : slot<GR>(a.ws.head, ba + k)));
+                q = GR::warp_reduce(q);
+                if (lane == 0) {
+                    GR::store(a.out, s, q, f64);
+                    GR::store_aux(a.argidx, a.aux, s, q, sb);
+                    a.ws.seg_cnt[ba] = 0u;
+                }
+            }
+            __syncthreads();
+        };
+
+        // Tiles lying wholly inside [P0, P1) are "interior": their vectors are
+        // loaded one tile ahead, so loads stay in flight through the block
+        // combines at segment boundaries (and through the search below).
+        auto interior = [&](int64_t t) {
+            const int64_t l = J0 + t * TILE - shift;
+            return l >= P0 && l + TILE <= P1;
+        };
+        auto load_tile = [&](int64_t t, Words<VB> (&w)[U]) {
+            const int64_t l = J0 + t * TILE - shift;
+#pragma unroll
+            for (int u = 0; u < U; u++) w[u] = ldv<VB>(x + l + ((int64_t)u * B + threadIdx.x) * VE);
+        };
+        Words<VB> wn[U];
+        bool have = t0 < t1 && interior(t0);
+        if (have) load_tile(t0, wn);
+
+        if (warp == 0) {
+            const int64_t r = sg.find(0, blk_lo, lane);
+            if (lane == 0) s_i64 = r;
+        }
+        __syncthreads();
+        int64_t cs = s_i64;
+        int64_t cend = sg.end(cs);
+
+        Acc acc[U];
 #pragma unroll
         for (int u = 0; u < U; u++) acc[u] = T::init();
-        const int64_t sb = sg.begin(s), se = sg.end(s);
-        if (sb >= blk_lo && se <= blk_hi) {
-            if (threadIdx.x == 0) {
-                T::store(a.out, s, p, f64);
-                T::store_aux(a.argidx, a.aux, s, p, sb);
-            }
-            return;
-        }
-        const int64_t ba = (sb + shift - J0) / CB, bb = (se - 1 + shift - J0) / CB;
-        if (threadIdx.x == 0) {
-            *slot<T>(sb < blk_lo ? a.ws.head : a.ws.tail, blockIdx.x) = p;
-            __threadfence();
-            const unsigned old = atomicAdd(a.ws.seg_cnt + ba, 1u);
-            s_fin = (old == (unsigned)(bb - ba));
-        }
-        __syncthreads();
-        if (s_fin && warp == 0) {
-            __threadfence();
-            Part q = T::part_init();
-            for (int64_t k = lane; k <= bb - ba; k += 32)
-                q = T::combine(q, ld_cg_any(k == 0 ? slot<T>(a.ws.tail, ba) : slot<T>(a.ws.head, ba + k)));
-            q = T::warp_reduce(q);
-            if (lane == 0) {
-                T::store(a.out, s, q, f64);
-                T::store_aux(a.argidx, a.aux, s, q, sb);
-                a.ws.seg_cnt[ba] = 0u;
-            }
-        }
-        __syncthreads();
-    };
 
-    if (threadIdx.x == 0) s_i64 = sg.find(0, blk_lo);
-    __syncthreads();
-    int64_t cs = s_i64;
-
-    Acc acc[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) acc[u] = T::init();
-
-    for (int64_t t = t0; t < t1; t++) {
-        const int64_t tlo = J0 + t * TILE - shift, thi = tlo + TILE;
-        const int64_t cend = sg.end(cs);
-        if (cend >= thi && tlo >= P0 && thi <= P1) {
-            // the whole tile lies inside segment cs: stream it
+        for (int64_t t = t0; t < t1; t++) {
+            const int64_t tlo = J0 + t * TILE - shift, thi = tlo + TILE;
             Words<VB> w[U];
 #pragma unroll
-            for (int u = 0; u < U; u++) w[u] = ldv<VB>(x + tlo + ((int64_t)u * B + threadIdx.x) * VE);
+            for (int u = 0; u < U; u++) w[u] = wn[u];
+            const bool cur = have;
+            have = t + 1 < t1 && interior(t + 1);
+            if (have) load_tile(t + 1, wn);
+            if (cur && cend >= thi) {
+                // the whole tile lies inside segment cs: stream it
 #pragma unroll
-            for (int u = 0; u < U; u++) {
-                E e[VE];
-                Ld::template dec<VB>(w[u], e);
-                T::add_vec(acc[u], e, tlo + ((int64_t)u * B + threadIdx.x) * VE);
+                for (int u = 0; u < U; u++) {
+                    E e[VE];
+                    Ld::template dec<VB>(w[u], e);
+                    T::add_vec(acc[u], e, tlo + ((int64_t)u * B + threadIdx.x) * VE);
+                }
+                continue;
             }
-            continue;
+            // accumulate positions [p0, p1) of this tile into ac
+            auto part = [&](Acc (&ac)[U], int64_t p0, int64_t p1) {
+                if (cur) masked_words<T, U, VB>(ac, w, tlo, p0, p1);
+                else ctx.masked(ac, tlo, p0, p1);
+            };
+            const int64_t lo = tlo > P0 ? tlo : P0, hi = thi < P1 ? thi : P1;
+            if (cend >= hi) {
+                part(acc, lo, hi);
+                continue;
+            }
+            // segment cs ends inside this tile
+            part(acc, lo, cend);
+            emit(cs, acc);
+            __syncthreads();
+            if (warp == 0) {
+                const int64_t r = sg.find(cs + 1, hi - 1, lane);
+                if (lane == 0) s_i64 = r;
+            }
+            __syncthreads();
+            const int64_t ns = s_i64;
+            // segments lying wholly inside the tile: short ones one per warp ...
+            for (int64_t s = cs + 1 + warp; s < ns; s += nwarps) {
+                const int64_t sb = sg.begin(s), se = sg.end(s);
+                if (se == sb || se - sb > kSmallSeg) continue;
+                Acc wa = T::init();
+                int64_t p = sb + lane;
+                for (; p + 96 < se; p += 128) {
+                    const E v0 = Ld::one(x, p), v1 = Ld::one(x, p + 32), v2 = Ld::one(x, p + 64), v3 = Ld::one(x, p + 96);
+                    T::add(wa, v0, p);
+                    T::add(wa, v1, p + 32);
+                    T::add(wa, v2, p + 64);
+                    T::add(wa, v3, p + 96);
+                }
+                for (; p < se; p += 32) T::add(wa, Ld::one(x, p), p);
+                const Part q = T::warp_reduce(T::to_part(wa));
+                if (lane == 0) {
+                    const G g = GR::up(q);
+                    GR::store(a.out, s, g, f64);
+                    GR::store_aux(a.argidx, a.aux, s, g, sb);
+                }
+            }
+            // ... long ones with the whole block
+            for (int64_t s = cs + 1; s < ns; s++) {
+                const int64_t sb = sg.begin(s), se = sg.end(s);
+                if (se - sb <= kSmallSeg) continue;
+                Acc ba_[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) ba_[u] = T::init();
+                part(ba_, sb, se);
+                const Part q = block_combine<T>(fold<T, U>(ba_));
+                if (threadIdx.x == 0) {
+                    const G g = GR::up(q);
+                    GR::store(a.out, s, g, f64);
+                    GR::store_aux(a.argidx, a.aux, s, g, sb);
+                }
+            }
+            cs = ns;
+            cend = sg.end(cs);
+            part(acc, sg.begin(ns), hi);
         }
-        const int64_t lo = tlo > P0 ? tlo : P0, hi = thi < P1 ? thi : P1;
-        if (cend >= hi) {
-            ctx.masked(acc, tlo, lo, hi);
-            continue;
-        }
-        // segment cs ends inside this tile
-        ctx.masked(acc, tlo, lo, cend);
         emit(cs, acc);
-        __syncthreads();
-        if (threadIdx.x == 0) s_i64 = sg.find(cs + 1, hi - 1);
-        __syncthreads();
-        const int64_t ns = s_i64;
-        // segments lying wholly inside the tile: short ones one per warp ...
-        for (int64_t s = cs + 1 + warp; s < ns; s += nwarps) {
-            const int64_t sb = sg.begin(s), se = sg.end(s);
-            if (se == sb || se - sb > kSmallSeg) continue;
-            Acc wa = T::init();
-            int64_t p = sb + lane;
-            for (; p + 96 < se; p += 128) {
-                const E v0 = Ld::one(x, p), v1 = Ld::one(x, p + 32), v2 = Ld::one(x, p + 64), v3 = Ld::one(x, p + 96);
-                T::add(wa, v0, p);
-                T::add(wa, v1, p + 32);
-                T::add(wa, v2, p + 64);
-                T::add(wa, v3, p + 96);
-            }
-            for (; p < se; p += 32) T::add(wa, Ld::one(x, p), p);
-            const Part q = T::warp_reduce(T::to_part(wa));
-            if (lane == 0) {
-                T::store(a.out, s, q, f64);
-                T::store_aux(a.argidx, a.aux, s, q, sb);
-            }
-        }
-        // ... long ones with the whole block
-        for (int64_t s = cs + 1; s < ns; s++) {
-            const int64_t sb = sg.begin(s), se = sg.end(s);
-            if (se - sb <= kSmallSeg) continue;
-            Acc ba_[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) ba_[u] = T::init();
-            ctx.masked(ba_, tlo, sb, se);
-            const Part q = block_combine<T>(fold<T, U>(ba_));
-            if (threadIdx.x == 0) {
-                T::store(a.out, s, q, f64);
-                T::store_aux(a.argidx, a.aux, s, q, sb);
-            }
-        }
-        cs = ns;
-        ctx.masked(acc, tlo, sg.begin(ns), hi);
     }
-    emit(cs, acc);
+    // the last block out re-arms the chunk counter for the next launch
+    if (a.dynamic_chunks && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.ws.blk_done, 1u) == gridDim.x - 1) {
+            *a.ws.chunk_ctr = 0u;
+            *a.ws.blk_done = 0u;
+        }
+    }
 }
 
 }  // namespace pr

@@ -172,15 +172,18 @@ struct SumF {
 // Neumaier-compensated sum (Section 1.1, second footnote: Kahan-style
 // compensation).  Per thread: kLanes independent fp32 (sum, compensation)
 // pairs, element k of a vector going to lane k mod kLanes (independent
-// dependency chains); across lanes, threads and blocks: the same algorithm in
-// fp64; one rounding at the end.
+// dependency chains).  Lanes, threads and warps combine as fp32 pairs with the
+// same algorithm; only the cross-block combine of block partials runs in fp64
+// (GridPart) -- GB300 issues fp64 adds at ~0.5e12/s, so fp64 inside the block
+// would cost more than the whole HBM stream.  One rounding at the end.
 template <class Ld_>
 struct SumComp {
     using Ld = Ld_;
     using E = typename Ld::E;
     static constexpr int kLanes = 4;
     struct Acc { float s[kLanes], c[kLanes]; };
-    struct Part { double s, c; };
+    struct Part { float s, c; };
+    struct GridPart { double s, c; };
     static constexpr bool kIdx = false;
     __device__ __forceinline__ static Acc init() {
         Acc a;
@@ -200,28 +203,38 @@ struct SumComp {
 #pragma unroll
         for (int k = 0; k < K; k++) neumaier(a.s[k % kLanes], a.c[k % kLanes], e[k]);
     }
-    __device__ __forceinline__ static Part part_init() { return {0.0, 0.0}; }
+    __device__ __forceinline__ static Part part_init() { return {0.f, 0.f}; }
     __device__ __forceinline__ static Part combine(const Part& a, const Part& b) {
-        const double t = a.s + b.s;
-        const double e = fabs(a.s) >= fabs(b.s) ? (a.s - t) + b.s : (b.s - t) + a.s;
+        const float t = a.s + b.s;
+        const float e = fabsf(a.s) >= fabsf(b.s) ? (a.s - t) + b.s : (b.s - t) + a.s;
         return {t, (a.c + b.c) + e};
     }
     __device__ __forceinline__ static Part to_part(const Acc& a) {
-        Part p{(double)a.s[0], (double)a.c[0]};
+        Part p{a.s[0], a.c[0]};
 #pragma unroll
-        for (int l = 1; l < kLanes; l++) p = combine(p, Part{(double)a.s[l], (double)a.c[l]});
+        for (int l = 1; l < kLanes; l++) p = combine(p, Part{a.s[l], a.c[l]});
         return p;
     }
     __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<SumComp>(p); }
-    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) {
-        // Once an infinity enters, s stays +-inf or NaN and the compensation
-        // turns NaN; the sum is then s itself.
-        const double r = isfinite(p.s) ? p.s + p.c : p.s;
+    // Once an infinity enters, s stays +-inf or NaN and the compensation turns
+    // NaN; the sum is then s itself.
+    __device__ __forceinline__ static void grid_store(void* out, int64_t i, const GridPart& g, bool f64) {
+        const double r = isfinite(g.s) ? g.s + g.c : g.s;
         if (f64) put_f64(out, i, r); else put_f32(out, i, (float)r);
+    }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) {
+        grid_store(out, i, to_grid(p), f64);
     }
     __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
     __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
         store(out, i, part_init(), f64);
+    }
+    __device__ __forceinline__ static GridPart to_grid(const Part& p) { return {(double)p.s, (double)p.c}; }
+    __device__ __forceinline__ static GridPart grid_init() { return {0.0, 0.0}; }
+    __device__ __forceinline__ static GridPart grid_combine(const GridPart& a, const GridPart& b) {
+        const double t = a.s + b.s;
+        const double e = fabs(a.s) >= fabs(b.s) ? (a.s - t) + b.s : (b.s - t) + a.s;
+        return {t, (a.c + b.c) + e};
     }
 };
 
@@ -532,6 +545,54 @@ struct ArgExt {
     }
 };
 
+// Float extremum plus first index, for f32 (and bf16 / f16 widened to f32):
+// a vector's extremum is taken with max.NaN / min.NaN (one instruction per
+// element); only when it can replace the running best is the vector searched
+// for the first element with the same key.  Same result as ArgExt<KeyF32>.
+template <class Ld_, int OutK, bool MX>
+struct ArgExtF {
+    using Ld = Ld_;
+    using E = float;
+    using Key = KeyF32<Ld_, OutK>;
+    using Base = ArgExt<Key, MX>;
+    using Acc = typename Base::Acc;
+    using Part = Acc;
+    static constexpr bool kIdx = true;
+    __device__ __forceinline__ static Acc init() { return Base::init(); }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t i) { Base::add(a, v, i); }
+    template <int N>
+    __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[N], int64_t i0) {
+        float t[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) t[k] = e[k];
+#pragma unroll
+        for (int s = 1; s < N; s <<= 1)
+#pragma unroll
+            for (int k = 0; k + s < N; k += 2 * s) t[k] = MaxMinF<Ld_, OutK, MX>::f(t[k], t[k + s]);
+        const uint32_t km = Key::key(t[0], MX);
+        // i0 bounds the vector's indices from below: if even that cannot win, nothing in it can
+        if (Base::better(km, i0, a.key, a.idx)) {
+            int kk = N - 1;
+#pragma unroll
+            for (int k = N - 1; k >= 0; k--)
+                if (Key::key(e[k], MX) == km) kk = k;
+            if (Base::better(km, i0 + kk, a.key, a.idx)) { a.key = km; a.idx = i0 + kk; }
+        }
+    }
+    __device__ __forceinline__ static Part to_part(const Acc& a) { return a; }
+    __device__ __forceinline__ static Part part_init() { return Base::part_init(); }
+    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return Base::combine(a, b); }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<ArgExtF>(p); }
+    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) { Base::store(out, i, p, f64); }
+    __device__ __forceinline__ static void store_aux(int64_t* argidx, pr_prod_aux* aux, int64_t i, const Part& p,
+                                                     int64_t seg_begin) {
+        Base::store_aux(argidx, aux, i, p, seg_begin);
+    }
+    __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t* argidx, pr_prod_aux* aux) {
+        Base::store_empty(out, i, f64, argidx, aux);
+    }
+};
+
 // ------------------------------------------------------------------------
 // PROD
 // ------------------------------------------------------------------------
@@ -573,10 +634,10 @@ struct ProdF {
 // fp64 product on the integer pipes.  GB300's fp64 units issue ~0.5e12
 // multiplies/s, slower than HBM delivers doubles (~0.9e12/s), so the combine
 // keeps a 64-bit significand m in [2^63, 2^64) and a 64-bit exponent e
-// (value = m * 2^(e-63)) and multiplies significands with four 32x32->64
-// integer multiplies, rounding the 128-bit product to nearest.  Each step
-// errs by at most 2^-64 relative (fp64: 2^-53), and there is no intermediate
-// overflow or underflow.  Zeros, infinities and NaNs are flags; the sign is
+// (value = m * 2^(e-63)) and multiplies significands with three 32x32->64
+// integer multiplies (mul_sig).  Each step errs by less than 2^-61 relative,
+// toward zero (fp64: 2^-53 either way), so n factors err by less than
+// n * 2^-61; there is no intermediate overflow or underflow.  Zeros, infinities and NaNs are flags; the sign is
 // the xor of all signs (the IEEE rule for multiplication).
 struct ProdExt {
     using Ld = LdF64;
@@ -587,22 +648,20 @@ struct ProdExt {
     static constexpr bool kIdx = false;
     static constexpr bool kOutF64 = true;
 
-    // m' = round(a*b / 2^(63+adj)), a, b in [2^63, 2^64); returns m' in [2^63, 2^64).
+    // m' = a*b / 2^(63+adj), truncated, for a, b in [2^63, 2^64); m' in [2^63, 2^64).
+    // Built from the three high 32x32->64 partial products: the low product
+    // a0*b0 (< 2^64) is dropped and the rest truncated, so each step errs by
+    // less than 2^-61 relative, toward zero, and is exact whenever the dropped
+    // bits are zero (e.g. a factor that is a power of two).  An fp64 multiply
+    // errs by up to 2^-53.
     __device__ __forceinline__ static uint64_t mul_sig(uint64_t a, uint64_t b, int& adj) {
         const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
-        const uint64_t p00 = (uint64_t)a0 * b0, p01 = (uint64_t)a0 * b1;
-        const uint64_t p10 = (uint64_t)a1 * b0, p11 = (uint64_t)a1 * b1;
-        const uint64_t mid = (p00 >> 32) + (uint32_t)p01 + (uint32_t)p10;
+        const uint64_t p01 = (uint64_t)a0 * b1, p10 = (uint64_t)a1 * b0, p11 = (uint64_t)a1 * b1;
+        const uint64_t mid = (uint64_t)(uint32_t)p01 + (uint32_t)p10;
         const uint64_t hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
-        const uint32_t lo_hi = (uint32_t)mid;  // bits 32..63 of the low 64-bit word
         const int top = (int)(hi >> 63);
-        uint64_t m = top ? hi : ((hi << 1) | (lo_hi >> 31));
-        const uint32_t rb = top ? (lo_hi >> 31) : ((lo_hi >> 30) & 1u);
-        m += rb;
-        const int ovf = (m == 0);  // rounding carried out of bit 63
-        m = ovf ? 0x8000000000000000ull : m;
-        adj = top + ovf;
-        return m;
+        adj = top;
+        return top ? hi : ((hi << 1) | ((uint32_t)mid >> 31));
     }
     __device__ __forceinline__ static Acc init() { Acc a; a.m = 0x8000000000000000ull; a.e = 0; a.f = 0; a.pad_ = 0; return a; }
 
@@ -705,10 +764,29 @@ struct ProdAux {
             Base::add(a.p, v, i);
         }
     }
+    // Zeros are replaced by 1 for the product (so the vector multiplies as a
+    // tree in the base trait); the zero bookkeeping runs only for vectors that
+    // contain a zero.
     template <int K>
     __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t i0) {
+        E t[K];
+        bool any = false;
 #pragma unroll
-        for (int k = 0; k < K; k++) add(a, e[k], i0 + k);
+        for (int k = 0; k < K; k++) {
+            const bool z = e[k] == (E)0;
+            any |= z;
+            t[k] = z ? (E)1 : e[k];
+        }
+        Base::add_vec(a.p, t, i0);
+        if (any) {
+#pragma unroll
+            for (int k = 0; k < K; k++)
+                if (e[k] == (E)0) {
+                    a.zc += 1;
+                    a.zi = i0 + k < a.zi ? i0 + k : a.zi;
+                    a.zsign ^= (uint32_t)(signbit(e[k]) != 0);
+                }
+        }
     }
     __device__ __forceinline__ static Part to_part(const Acc& a) {
         Part r; r.p = Base::to_part(a.p); r.zc = a.zc; r.zi = a.zi; r.zsign = a.zsign; r.pad_ = 0; return r;

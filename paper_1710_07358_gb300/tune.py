@@ -44,6 +44,46 @@ def _data(torch, dtype, op, n, g):
     return torch.randint(-(1 << 62), 1 << 62, (n,), generator=g, device=dev, dtype=torch.int64)
 
 
+def tune_backward(torch, rows=64, cols=1 << 20, reps=5):
+    """Pick the backward kernel's launch shape by timing pr_reduce_backward (SUM)
+    with CUDA events over the candidate space; the winner is set for every
+    differentiable op of the dtype at this size bucket."""
+    best = {}
+    for dtype in ("f32", "f64"):
+        tdt = pr.torch_dtype(dtype)
+        x = torch.zeros(rows, cols, dtype=tdt, device="cuda")
+        g = torch.ones(rows, dtype=tdt, device="cuda")
+        gi = torch.empty_like(x)
+        n = rows * cols
+        results = []
+        for block in (256, 512, 1024):
+            for bps in (1, 2, 4, 8):
+                if block * bps > 2048:
+                    continue
+                for unroll in (2, 4):
+                    for vb in (16, 32):
+                        cfg = dict(block=block, blocks_per_sm=bps, unroll=unroll, vec_bytes=vb)
+                        pr.set_config("backward", dtype, "sum", "plain", n, cfg)
+                        for _ in range(2):
+                            pr.reduce_backward("sum", x, g, out=gi)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        ts = []
+                        for _ in range(reps):
+                            e0.record()
+                            pr.reduce_backward("sum", x, g, out=gi)
+                            e1.record()
+                            e1.synchronize()
+                            ts.append(e0.elapsed_time(e1))
+                        results.append((min(ts), cfg))
+        t, cfg = min(results, key=lambda r: r[0])
+        for op in ("sum", "max", "min", "prod"):
+            pr.set_config("backward", dtype, op, "plain", n, cfg)
+        best[dtype] = (t, cfg)
+        print("backward %dx%d %s: %.1f us %s" % (rows, cols, dtype, t * 1e3, cfg), flush=True)
+        del x, gi
+    return best
+
+
 def main():
     import torch
     from . import synth
@@ -80,6 +120,15 @@ def main():
     for prec in ("compensated", "fp64_combine"):
         cfg = pr.autotune("segmented", xv, "sum", precision=prec, offsets=ov)
         print("segmented 4096 f32 sum %s: %s" % (prec, cfg), flush=True)
+    del xv, ov
+    # row reductions of the differentiation workload (64 rows of 2^20)
+    xr = torch.randn(64, 1 << 20, generator=g, device="cuda")
+    offr = torch.arange(0, 65, dtype=torch.int64, device="cuda") * (1 << 20)
+    for op in ("sum", "max", "prod"):
+        cfg = pr.autotune("segmented", xr.view(-1), op, offsets=offr)
+        print("rows 64x2^20 f32 %s: %s" % (op, cfg), flush=True)
+    del xr
+    tune_backward(torch)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     pr.check(pr.pr_tune_save(args.out))
     print("saved", args.out)

@@ -123,6 +123,9 @@ def test_config_roundtrip_and_validation(L):
     assert got.as_dict() == c.as_dict()
     for bad in ((100, 2, 4, 16), (512, 0, 4, 16), (512, 2, 3, 16), (512, 2, 4, 8), (2048, 1, 4, 16)):
         assert pr.pr_set_config(0, F32, SUM, PLAIN, 1, ctypes.byref(pr.pr_config(*bad))) == INVALID
+    # the segmented kernel runs blocks of at most 512 threads
+    assert pr.pr_set_config(1, F32, SUM, PLAIN, 1, ctypes.byref(pr.pr_config(1024, 1, 4, 32))) == INVALID
+    assert pr.pr_set_config(1, F32, SUM, PLAIN, 1, ctypes.byref(pr.pr_config(512, 1, 4, 32))) == OK
 
 
 def test_valid_call_without_a_gpu_fails_loudly(L):

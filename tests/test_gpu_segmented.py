@@ -206,7 +206,7 @@ def test_every_config_variant():
     o = dev_off(off)
     old = pr.get_config("segmented", "f32", "max", "plain", 300)
     try:
-        for block in (128, 512, 1024):
+        for block in (128, 256, 512):
             for unroll in (2, 4):
                 for vb in (16, 32):
                     pr.set_config("segmented", "f32", "max", "plain", 300,
