@@ -193,6 +193,10 @@ def forms(steps, warmup, peak, only=None, tune=True):
     if "plain" in want:
         for op in ("sum", "max", "min"):
             plain("f32_%s" % op, f32, op)
+        nb = f32.numel() * 4
+        _, per = time_launches(lambda: pr.reduce_arg(f32, "max"), k, warmup, st)
+        res["f32_argmax"] = {"GB/s": round(gbs(nb, per), 1), "frac": round(gbs(nb, per) / peak, 4),
+                             "us": round(per * 1e3, 2)}
         i32 = torch.randint(-(1 << 20), 1 << 20, (n,), generator=g, device=dev, dtype=torch.int32)
         for op in ("sum", "max", "min"):
             plain("i32_%s" % op, i32, op)

@@ -75,8 +75,10 @@ typedef enum {
 /* Precision of floating-point SUM (Section 1.1, second footnote: use double
  * precision or Kahan-style compensation to cut the accumulated error).
  *   PLAIN          per-thread fp32 accumulators, fp32 combines (fp64 input: fp64).
- *   COMPENSATED    per-thread Neumaier (sum, compensation) pairs in fp32, combined
- *                  across threads and blocks in fp64 Neumaier, rounded once.
+ *   COMPENSATED    per-thread fp32 (sum, compensation) pairs, each element added
+ *                  with its exact rounding error (TwoSum); pairs combined within
+ *                  a block with Neumaier's algorithm in fp32 and across blocks in
+ *                  fp64; rounded once.
  *   FP64_COMBINE   per-thread fp32 accumulators, fp64 warp/block/grid combine. */
 typedef enum {
     PR_PREC_PLAIN = 0, PR_PREC_COMPENSATED = 1, PR_PREC_FP64_COMBINE = 2
@@ -121,6 +123,15 @@ pr_status pr_reduce(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* ou
 pr_status pr_reduce_ex(const void* x, int64_t n, pr_dtype dtype, pr_op op,
                        pr_precision precision, pr_dtype out_dtype, void* out,
                        pr_stream_t stream);
+
+/* (out[0], idx[0]) = (MAX or MIN of x[0..n), index of its first occurrence):
+ * argmax / argmin of a whole array, in one launch like pr_reduce.  Float
+ * inputs follow the MAX/MIN rules above (NaN is the extremum, its first
+ * occurrence wins; -0 < +0).  out: one element of pr_out_dtype(dtype, op);
+ * idx: one int64, -1 for n == 0.  Other ops: PR_ERR_UNSUPPORTED.
+ *                         (Section 1.1's combiner on (value, index) pairs) */
+pr_status pr_reduce_arg(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* out,
+                        int64_t* idx, pr_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
 /* Segmented reduction: many independent reductions in one launch           */

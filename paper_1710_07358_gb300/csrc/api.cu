@@ -237,8 +237,9 @@ static pr_status persistent_grid(const KernelEntry* e, const pr_config& c, int s
 // ------------------------------------------------------------------------
 
 static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int prec, bool out_f64, void* out,
-                            void* part_out, cudaStream_t st, const pr_config& c) {
-    const KernelEntry* e = reg_find(KernelKey{K_REDUCE, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec, AUX_NONE,
+                            void* part_out, cudaStream_t st, const pr_config& c, int aux = AUX_NONE,
+                            int64_t* argidx = nullptr) {
+    const KernelEntry* e = reg_find(KernelKey{K_REDUCE, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec, (uint8_t)aux,
                                               (uint8_t)c.unroll, (uint8_t)c.vec_bytes});
     if (!e) return fail(PR_ERR_UNSUPPORTED, "no reduce kernel for dtype %d op %d precision %d", dtype, op, prec);
     DevInfo di;
@@ -258,7 +259,7 @@ static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int pre
     const uintptr_t addr = reinterpret_cast<uintptr_t>(x);
     int64_t head = (int64_t)(((uintptr_t)c.vec_bytes - addr % (uintptr_t)c.vec_bytes) % (uintptr_t)c.vec_bytes) / es;
     if (head > n) head = n;
-    ReduceArgs a{x, n, head, out, part_out, out_f64 ? 1 : 0, ws};
+    ReduceArgs a{x, n, head, out, part_out, out_f64 ? 1 : 0, ws, argidx};
     cudaError_t err = reinterpret_cast<ReduceLaunch>(e->launch)(a, grid, c.block, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "reduce launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -402,6 +403,21 @@ pr_status pr_reduce_ex(const void* x, int64_t n, pr_dtype dtype, pr_op op, pr_pr
     ensure_registered();
     const pr_config c = lookup_cfg(PR_KIND_REDUCE, dtype, op, precision, n);
     return run_reduce(x, n, dtype, op, precision, f64, out, nullptr, (cudaStream_t)stream, c);
+}
+
+pr_status pr_reduce_arg(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* out, int64_t* idx,
+                        pr_stream_t stream) {
+    g_msg.clear();
+    pr_status s = check_common(dtype, op, PR_PREC_PLAIN);
+    if (s != PR_OK) return s;
+    if (op != PR_MAX && op != PR_MIN) return fail(PR_ERR_UNSUPPORTED, "arg-extremum needs MAX or MIN");
+    if (n < 0) return fail(PR_ERR_INVALID, "n must be >= 0 (got %lld)", (long long)n);
+    if (!x && n > 0) return fail(PR_ERR_INVALID, "x is NULL");
+    if (!out || !idx) return fail(PR_ERR_INVALID, "out / idx is NULL");
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    ensure_registered();
+    const pr_config c = lookup_cfg(PR_KIND_REDUCE, dtype, op, PR_PREC_PLAIN, n);
+    return run_reduce(x, n, dtype, op, PR_PREC_PLAIN, false, out, nullptr, (cudaStream_t)stream, c, AUX_ARG, idx);
 }
 
 pr_status pr_reduce(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* out, pr_stream_t stream) {

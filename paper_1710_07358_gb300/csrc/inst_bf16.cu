@@ -10,7 +10,7 @@ void register_bf16() {
     reg_family<ProdF<LdBF16>>(PR_BF16, PR_PROD, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMinF<LdBF16, 1, true>>(PR_BF16, PR_MAX, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMinF<LdBF16, 1, false>>(PR_BF16, PR_MIN, PR_PREC_PLAIN, AUX_NONE, true, true);
-    reg_family<ArgExtF<LdBF16, 1, true>>(PR_BF16, PR_MAX, PR_PREC_PLAIN, AUX_ARG, false, true);
-    reg_family<ArgExtF<LdBF16, 1, false>>(PR_BF16, PR_MIN, PR_PREC_PLAIN, AUX_ARG, false, true);
+    reg_family<ArgExtF<LdBF16, 1, true>>(PR_BF16, PR_MAX, PR_PREC_PLAIN, AUX_ARG, true, true);
+    reg_family<ArgExtF<LdBF16, 1, false>>(PR_BF16, PR_MIN, PR_PREC_PLAIN, AUX_ARG, true, true);
 }
 }  // namespace pr

@@ -10,7 +10,7 @@ void register_f16() {
     reg_family<ProdF<LdF16>>(PR_F16, PR_PROD, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMinF<LdF16, 2, true>>(PR_F16, PR_MAX, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMinF<LdF16, 2, false>>(PR_F16, PR_MIN, PR_PREC_PLAIN, AUX_NONE, true, true);
-    reg_family<ArgExtF<LdF16, 2, true>>(PR_F16, PR_MAX, PR_PREC_PLAIN, AUX_ARG, false, true);
-    reg_family<ArgExtF<LdF16, 2, false>>(PR_F16, PR_MIN, PR_PREC_PLAIN, AUX_ARG, false, true);
+    reg_family<ArgExtF<LdF16, 2, true>>(PR_F16, PR_MAX, PR_PREC_PLAIN, AUX_ARG, true, true);
+    reg_family<ArgExtF<LdF16, 2, false>>(PR_F16, PR_MIN, PR_PREC_PLAIN, AUX_ARG, true, true);
 }
 }  // namespace pr

@@ -10,8 +10,8 @@ void register_f32_seg() {
     reg_family<ProdF<LdF32>>(PR_F32, PR_PROD, PR_PREC_PLAIN, AUX_NONE, false, true);
     reg_family<MaxMinF<LdF32, 0, true>>(PR_F32, PR_MAX, PR_PREC_PLAIN, AUX_NONE, false, true);
     reg_family<MaxMinF<LdF32, 0, false>>(PR_F32, PR_MIN, PR_PREC_PLAIN, AUX_NONE, false, true);
-    reg_family<ArgExtF<LdF32, 0, true>>(PR_F32, PR_MAX, PR_PREC_PLAIN, AUX_ARG, false, true);
-    reg_family<ArgExtF<LdF32, 0, false>>(PR_F32, PR_MIN, PR_PREC_PLAIN, AUX_ARG, false, true);
+    reg_family<ArgExtF<LdF32, 0, true>>(PR_F32, PR_MAX, PR_PREC_PLAIN, AUX_ARG, true, true);
+    reg_family<ArgExtF<LdF32, 0, false>>(PR_F32, PR_MIN, PR_PREC_PLAIN, AUX_ARG, true, true);
     reg_family<ProdAux<ProdF<LdF32>>>(PR_F32, PR_PROD, PR_PREC_PLAIN, AUX_PROD, false, true);
 }
 }  // namespace pr

@@ -8,8 +8,8 @@ void register_f64() {
     reg_family<ProdExt>(PR_F64, PR_PROD, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMin<KeyF64, true>>(PR_F64, PR_MAX, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMin<KeyF64, false>>(PR_F64, PR_MIN, PR_PREC_PLAIN, AUX_NONE, true, true);
-    reg_family<ArgExt<KeyF64, true>>(PR_F64, PR_MAX, PR_PREC_PLAIN, AUX_ARG, false, true);
-    reg_family<ArgExt<KeyF64, false>>(PR_F64, PR_MIN, PR_PREC_PLAIN, AUX_ARG, false, true);
+    reg_family<ArgExt<KeyF64, true>>(PR_F64, PR_MAX, PR_PREC_PLAIN, AUX_ARG, true, true);
+    reg_family<ArgExt<KeyF64, false>>(PR_F64, PR_MIN, PR_PREC_PLAIN, AUX_ARG, true, true);
     reg_family<ProdAux<ProdExt>>(PR_F64, PR_PROD, PR_PREC_PLAIN, AUX_PROD, false, true);
 }
 }  // namespace pr

@@ -10,7 +10,7 @@ void register_i64() {
     reg_family<IntOp<LdI64, uint64_t, 6>>(PR_I64, PR_XOR, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMin<KeyI64, true>>(PR_I64, PR_MAX, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMin<KeyI64, false>>(PR_I64, PR_MIN, PR_PREC_PLAIN, AUX_NONE, true, true);
-    reg_family<ArgExt<KeyI64, true>>(PR_I64, PR_MAX, PR_PREC_PLAIN, AUX_ARG, false, true);
-    reg_family<ArgExt<KeyI64, false>>(PR_I64, PR_MIN, PR_PREC_PLAIN, AUX_ARG, false, true);
+    reg_family<ArgExt<KeyI64, true>>(PR_I64, PR_MAX, PR_PREC_PLAIN, AUX_ARG, true, true);
+    reg_family<ArgExt<KeyI64, false>>(PR_I64, PR_MIN, PR_PREC_PLAIN, AUX_ARG, true, true);
 }
 }  // namespace pr

@@ -10,7 +10,7 @@ void register_u32() {
     reg_family<IntOp<LdU32, uint32_t, 6>>(PR_U32, PR_XOR, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMin<KeyU32, true>>(PR_U32, PR_MAX, PR_PREC_PLAIN, AUX_NONE, true, true);
     reg_family<MaxMin<KeyU32, false>>(PR_U32, PR_MIN, PR_PREC_PLAIN, AUX_NONE, true, true);
-    reg_family<ArgExt<KeyU32, true>>(PR_U32, PR_MAX, PR_PREC_PLAIN, AUX_ARG, false, true);
-    reg_family<ArgExt<KeyU32, false>>(PR_U32, PR_MIN, PR_PREC_PLAIN, AUX_ARG, false, true);
+    reg_family<ArgExt<KeyU32, true>>(PR_U32, PR_MAX, PR_PREC_PLAIN, AUX_ARG, true, true);
+    reg_family<ArgExt<KeyU32, false>>(PR_U32, PR_MIN, PR_PREC_PLAIN, AUX_ARG, true, true);
 }
 }  // namespace pr

@@ -59,6 +59,7 @@ struct ReduceArgs {
     void* part_out;      // non-null: store the final Part here instead of a result
     int out_f64;
     Workspace ws;
+    int64_t* argidx;     // arg-extremum traits: index of the first extremum (may be null)
 };
 
 struct SegArgs {
@@ -122,6 +123,7 @@ __device__ __forceinline__ typename T::Part* slot(char* base, int64_t i) {
     return reinterpret_cast<typename T::Part*>(base + i * kSlot);
 }
 
+// Combine a thread's U accumulators into one Part.
 template <class T, int U>
 __device__ __forceinline__ typename T::Part fold(typename T::Acc (&acc)[U]) {
     typename T::Part p = T::to_part(acc[0]);
@@ -192,8 +194,12 @@ __global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a) {
     for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) q = GR::combine(q, ld_cg_any(slot<GR>(a.ws.partials, j)));
     q = block_combine<GR>(q);
     if (threadIdx.x == 0) {
-        if (a.part_out) *static_cast<G*>(a.part_out) = q;
-        else GR::store(a.out, 0, q, a.out_f64 != 0);
+        if (a.part_out) {
+            *static_cast<G*>(a.part_out) = q;
+        } else {
+            GR::store(a.out, 0, q, a.out_f64 != 0);
+            GR::store_aux(a.argidx, nullptr, 0, q, 0);
+        }
         *a.ws.counter = 0u;
     }
 }

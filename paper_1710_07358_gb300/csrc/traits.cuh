@@ -169,11 +169,12 @@ struct SumF {
     }
 };
 
-// Neumaier-compensated sum (Section 1.1, second footnote: Kahan-style
-// compensation).  Per thread: kLanes independent fp32 (sum, compensation)
-// pairs, element k of a vector going to lane k mod kLanes (independent
-// dependency chains).  Lanes, threads and warps combine as fp32 pairs with the
-// same algorithm; only the cross-block combine of block partials runs in fp64
+// Compensated sum (Section 1.1, second footnote: Kahan-style compensation).
+// Per thread: kLanes independent fp32 (sum, compensation) pairs, element k of
+// a vector going to lane k mod kLanes (independent dependency chains), each
+// element added with TwoSum.  Lanes, threads and warps combine as fp32 pairs
+// with Neumaier's algorithm; only the cross-block combine of block partials
+// runs in fp64
 // (GridPart) -- GB300 issues fp64 adds at ~0.5e12/s, so fp64 inside the block
 // would cost more than the whole HBM stream.  One rounding at the end.
 template <class Ld_>
@@ -191,17 +192,22 @@ struct SumComp {
         for (int l = 0; l < kLanes; l++) { a.s[l] = 0.f; a.c[l] = 0.f; }
         return a;
     }
-    __device__ __forceinline__ static void neumaier(float& s, float& c, float v) {
+    // Per element: s + v with its exact rounding error (Knuth's TwoSum, six
+    // adds and no compare -- the same compensation as Neumaier's branch, but
+    // on the FMA pipe instead of the ALU pipe, which the compare and selects
+    // saturated for 16-bit inputs), the error accumulated in c.
+    __device__ __forceinline__ static void two_sum_acc(float& s, float& c, float v) {
         const float t = s + v;
-        if (fabsf(s) >= fabsf(v)) c = c + ((s - t) + v);
-        else c = c + ((v - t) + s);
+        const float bp = t - s;
+        const float ap = t - bp;
+        c = c + ((s - ap) + (v - bp));
         s = t;
     }
-    __device__ __forceinline__ static void add(Acc& a, E v, int64_t) { neumaier(a.s[0], a.c[0], v); }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t) { two_sum_acc(a.s[0], a.c[0], v); }
     template <int K>
     __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t) {
 #pragma unroll
-        for (int k = 0; k < K; k++) neumaier(a.s[k % kLanes], a.c[k % kLanes], e[k]);
+        for (int k = 0; k < K; k++) two_sum_acc(a.s[k % kLanes], a.c[k % kLanes], e[k]);
     }
     __device__ __forceinline__ static Part part_init() { return {0.f, 0.f}; }
     __device__ __forceinline__ static Part combine(const Part& a, const Part& b) {
@@ -751,45 +757,49 @@ template <class Base>
 struct ProdAux {
     using Ld = typename Base::Ld;
     using E = typename Ld::E;
-    struct Acc { typename Base::Acc p; int64_t zc; int64_t zi; uint32_t zsign; uint32_t pad_; };
+    // zsv: xor of the zeros' sign words (bit 31 is the sign of a +-0)
+    struct Acc { typename Base::Acc p; int64_t zi; uint32_t zc; uint32_t zsv; };
     struct Part { typename Base::Part p; int64_t zc; int64_t zi; uint32_t zsign; uint32_t pad_; };
     static constexpr bool kIdx = true;
-    __device__ __forceinline__ static Acc init() { Acc a; a.p = Base::init(); a.zc = 0; a.zi = INT64_MAX; a.zsign = 0; a.pad_ = 0; return a; }
+    __device__ __forceinline__ static uint32_t sign_word(E v) {
+        if constexpr (sizeof(E) == 8) return (uint32_t)((uint64_t)__double_as_longlong(v) >> 32);
+        else return __float_as_uint(v);
+    }
+    __device__ __forceinline__ static Acc init() { Acc a; a.p = Base::init(); a.zi = INT64_MAX; a.zc = 0; a.zsv = 0; return a; }
     __device__ __forceinline__ static void add(Acc& a, E v, int64_t i) {
         if (v == (E)0) {
             a.zc += 1;
             a.zi = i < a.zi ? i : a.zi;
-            a.zsign ^= (uint32_t)(signbit(v) != 0);
+            a.zsv ^= sign_word(v);
         } else {
             Base::add(a.p, v, i);
         }
     }
     // Zeros are replaced by 1 for the product (so the vector multiplies as a
-    // tree in the base trait); the zero bookkeeping runs only for vectors that
-    // contain a zero.
+    // tree in the base trait); the zero count, first zero and zero signs come
+    // from a bit mask without per-element branches.
     template <int K>
     __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t i0) {
+        static_assert(K <= 32, "zero mask is one word");
         E t[K];
-        bool any = false;
+        uint32_t mask = 0, sx = 0;
 #pragma unroll
         for (int k = 0; k < K; k++) {
             const bool z = e[k] == (E)0;
-            any |= z;
             t[k] = z ? (E)1 : e[k];
+            mask |= (uint32_t)z << k;
+            sx ^= z ? sign_word(e[k]) : 0u;
         }
         Base::add_vec(a.p, t, i0);
-        if (any) {
-#pragma unroll
-            for (int k = 0; k < K; k++)
-                if (e[k] == (E)0) {
-                    a.zc += 1;
-                    a.zi = i0 + k < a.zi ? i0 + k : a.zi;
-                    a.zsign ^= (uint32_t)(signbit(e[k]) != 0);
-                }
+        a.zc += __popc(mask);
+        a.zsv ^= sx;
+        if (mask) {
+            const int64_t i = i0 + __ffs(mask) - 1;
+            a.zi = i < a.zi ? i : a.zi;
         }
     }
     __device__ __forceinline__ static Part to_part(const Acc& a) {
-        Part r; r.p = Base::to_part(a.p); r.zc = a.zc; r.zi = a.zi; r.zsign = a.zsign; r.pad_ = 0; return r;
+        Part r; r.p = Base::to_part(a.p); r.zc = a.zc; r.zi = a.zi; r.zsign = a.zsv >> 31; r.pad_ = 0; return r;
     }
     __device__ __forceinline__ static Part part_init() { return to_part(init()); }
     __device__ __forceinline__ static Part combine(const Part& a, const Part& b) {

@@ -50,6 +50,7 @@ _P, _I64, _I32, _I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_i
 _SIGS = {
     "pr_reduce": [_P, _I64, _I, _I, _P, _P],
     "pr_reduce_ex": [_P, _I64, _I, _I, _I, _I, _P, _P],
+    "pr_reduce_arg": [_P, _I64, _I, _I, _P, _P, _P],
     "pr_segmented_reduce": [_P, _P, _I64, _I, _I, _P, _P],
     "pr_segmented_reduce_aux": [_P, _P, _I64, _I, _I, _I, _P, _P, _P, _P],
     "pr_reduce_rows": [_P, _I64, _I64, _I, _I, _I, _P, _P, _P, _P],
@@ -114,6 +115,10 @@ def pr_reduce(x, n, dtype, op, out, stream):
 
 def pr_reduce_ex(x, n, dtype, op, precision, out_dtype, out, stream):
     return lib().pr_reduce_ex(x, n, dtype, op, precision, out_dtype, out, stream)
+
+
+def pr_reduce_arg(x, n, dtype, op, out, idx, stream):
+    return lib().pr_reduce_arg(x, n, dtype, op, out, idx, stream)
 
 
 def pr_segmented_reduce(x, offsets, nseg, dtype, op, out, stream):
@@ -248,6 +253,19 @@ def reduce(x, op: str, precision: str = "plain", out_dtype: str | None = None, o
     check(pr_reduce_ex(_ptr(x), x.numel(), DTYPES[d], OPS[op], PRECISIONS[precision], DTYPES[od],
                        _ptr(out), _stream(x, stream)))
     return out
+
+
+def reduce_arg(x, op: str, stream=None):
+    """(0-d value tensor, 0-d int64 index tensor): max or min of x and the index
+    of its first occurrence."""
+    torch = _torch()
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("reduce_arg() needs a contiguous CUDA tensor")
+    d = dtype_name(x)
+    out = torch.empty((), dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
+    idx = torch.empty((), dtype=torch.int64, device=x.device)
+    check(pr_reduce_arg(_ptr(x), x.numel(), DTYPES[d], OPS[op], _ptr(out), _ptr(idx), _stream(x, stream)))
+    return out, idx
 
 
 def segmented_reduce(x, offsets, op: str, precision: str = "plain", argidx: bool = False,

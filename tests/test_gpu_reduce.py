@@ -248,3 +248,44 @@ def test_host_memory_path():
             assert got & mask == want & mask
     big = synth.uniform_i32((200 << 20) // 4 + 11, 62)       # four chunks
     assert pr.reduce_host(torch.from_numpy(big).pin_memory(), "sum") == oracle.reduce(big, "i32", "sum")
+
+
+ARG_DTYPES = ["f32", "f16", "bf16", "f64", "i32", "u32", "i64"]
+
+
+@pytest.mark.parametrize("dtype", ARG_DTYPES)
+@pytest.mark.parametrize("op", ["max", "min"])
+def test_reduce_arg_first_index(dtype, op):
+    """Whole-array arg-extremum: the extremum and its first index, with ties."""
+    for k, (n, offset) in enumerate([(0, 0), (1, 0), (37, 1), (4097, 3), ((1 << 20) + 3, 0), (5_533_214, 1)]):
+        if dtype in ("i32", "u32", "i64"):
+            x = {"i32": synth.uniform_i32(n, k, -50, 50), "u32": synth.uniform_i32(n, k, 0, 100).astype(np.uint32),
+                 "i64": synth.uniform_i32(n, k, -50, 50).astype(np.int64)}[dtype]
+        else:
+            x = gen(dtype, "max", n, k)
+        if n > 10:                       # plant a tie for the extremum: two positions, first must win
+            v = oracle.argext(x, dtype, op)[0]
+            x = np.array(x, copy=True)
+            x.reshape(-1)[n // 3] = x.reshape(-1)[oracle.argext(x, dtype, op)[1]]
+        t = to_device(x, dtype, offset)
+        val, idx = pr.reduce_arg(t, op)
+        wv, wi = oracle.argext(x, dtype, op)
+        got = values_of(val, pr.out_dtype_name(dtype, op))[0]
+        assert int(idx.item()) == wi, (n, int(idx.item()), wi)
+        if isinstance(got, int):
+            assert got == int(wv)
+        else:
+            assert same_float(got, wv)
+
+
+def test_reduce_arg_nan_and_signed_zero():
+    x = synth.uniform_f32(100003, 3)
+    x[[50000, 77]] = np.nan
+    v, i = pr.reduce_arg(to_device(x, "f32"), "max")
+    assert math.isnan(v.item()) and i.item() == 77
+    z = np.zeros(10001, np.float32)
+    z[:5000] = -0.0
+    v, i = pr.reduce_arg(to_device(z, "f32"), "max")
+    assert same_float(v.item(), 0.0) and i.item() == 5000
+    v, i = pr.reduce_arg(to_device(z, "f32"), "min")
+    assert same_float(v.item(), -0.0) and i.item() == 0

@@ -226,3 +226,33 @@ def test_malformed_offsets_raise_device_error_and_recover():
     good = [0, 10, 20, 64]
     vals, _ = run_seg(synth.normal_f32(64, 23), good, "f32", "sum")
     check_segments(synth.normal_f32(64, 23), good, "f32", "sum", vals)
+
+
+@pytest.mark.parametrize("rows,cols,offset", [(10000, 37, 1), (3, (1 << 21) + 5, 3), (1, 1 << 22, 0),
+                                              (64, 4096, 2), (700, 1000, 0)])
+def test_row_kernel_shapes(rows, cols, offset):
+    """Many short rows (one item per row) and few long rows split into column
+    chunks combined through per-row tickets, at several alignments."""
+    x = synth.normal_f32(rows * cols, rows + cols)
+    t = to_device(x, "f32", offset).view(rows, cols)
+    off = np.arange(rows + 1, dtype=np.int64) * cols
+    for op in ("sum", "max", "min"):
+        if op == "sum":
+            out = pr.reduce_rows(t, op)
+            check_segments(x, off, "f32", op, values_of(out, "f32"))
+        else:
+            out, ai = pr.reduce_rows(t, op, argidx=True)
+            check_segments(x, off, "f32", op, values_of(out, "f32"), argidx=ai.cpu().numpy())
+    xp = synth.uniform_f32(rows * cols, 7, 1 - 2.0 ** -7, 1 + 2.0 ** -7)
+    xp[::997] = 0.0
+    tp = to_device(xp, "f32", offset).view(rows, cols)
+    out, ax = pr.reduce_rows(tp, "prod", aux=True)
+    p_nz, zc, zi = (v.cpu().numpy() for v in pr.prod_aux_fields(ax))
+    vals = values_of(out, "f32")
+    for r in list(range(min(rows, 20))) + [rows - 1]:
+        seg = xp[r * cols:(r + 1) * cols]
+        wp, wz, wi = oracle.prod_aux(seg, "f32")
+        assert zc[r] == wz and zi[r] == wi
+        assert abs(p_nz[r] - wp) <= prod_rel_bound(cols, "f32") * abs(wp)
+        want = oracle.reduce(seg, "f32", "prod")
+        assert abs(vals[r] - want) <= prod_rel_bound(cols, "f32") * abs(want)
