@@ -416,7 +416,9 @@ pr_status pr_reduce_arg(const void* x, int64_t n, pr_dtype dtype, pr_op op, void
     if (!out || !idx) return fail(PR_ERR_INVALID, "out / idx is NULL");
     if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
     ensure_registered();
-    const pr_config c = lookup_cfg(PR_KIND_REDUCE, dtype, op, PR_PREC_PLAIN, n);
+    // The (key, index) accumulator wants more resident threads than plain
+    // max/min, whose tuned shapes it would otherwise share: use the default.
+    const pr_config c = default_cfg(PR_KIND_REDUCE, dtype, op, PR_PREC_PLAIN);
     return run_reduce(x, n, dtype, op, PR_PREC_PLAIN, false, out, nullptr, (cudaStream_t)stream, c, AUX_ARG, idx);
 }
 

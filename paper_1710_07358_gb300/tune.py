@@ -84,6 +84,48 @@ def tune_backward(torch, rows=64, cols=1 << 20, reps=5):
     return best
 
 
+def tune_rows(torch, rows=64, cols=1 << 20, reps=5):
+    """Row reductions as autograd runs them (argidx for max/min, product aux for
+    prod): time every segmented-kernel candidate with CUDA events and keep the
+    fastest for the (rows) bucket."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2)
+    x = torch.randn(rows, cols, generator=g, device="cuda")
+    for op in ("sum", "max", "min", "prod"):
+        results = []
+        for block in (128, 256, 512):
+            for bps in (1, 2, 4, 8):
+                if block * bps > 2048:
+                    continue
+                for unroll in (2, 4):
+                    for vb in (16, 32):
+                        cfg = dict(block=block, blocks_per_sm=bps, unroll=unroll, vec_bytes=vb)
+                        pr.set_config("segmented", "f32", op, "plain", rows, cfg)
+
+                        def run():
+                            if op in ("max", "min"):
+                                pr.reduce_rows(x, op, argidx=True)
+                            elif op == "prod":
+                                pr.reduce_rows(x, op, aux=True)
+                            else:
+                                pr.reduce_rows(x, op)
+                        run()
+                        run()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        ts = []
+                        for _ in range(reps):
+                            e0.record()
+                            run()
+                            e1.record()
+                            e1.synchronize()
+                            ts.append(e0.elapsed_time(e1))
+                        results.append((min(ts), cfg))
+        t, cfg = min(results, key=lambda r: r[0])
+        pr.set_config("segmented", "f32", op, "plain", rows, cfg)
+        print("rows %dx%d f32 %s: %.1f us %s" % (rows, cols, op, t * 1e3, cfg), flush=True)
+    del x
+
+
 def main():
     import torch
     from . import synth
@@ -122,12 +164,7 @@ def main():
         print("segmented 4096 f32 sum %s: %s" % (prec, cfg), flush=True)
     del xv, ov
     # row reductions of the differentiation workload (64 rows of 2^20)
-    xr = torch.randn(64, 1 << 20, generator=g, device="cuda")
-    offr = torch.arange(0, 65, dtype=torch.int64, device="cuda") * (1 << 20)
-    for op in ("sum", "max", "prod"):
-        cfg = pr.autotune("segmented", xr.view(-1), op, offsets=offr)
-        print("rows 64x2^20 f32 %s: %s" % (op, cfg), flush=True)
-    del xr
+    tune_rows(torch)
     tune_backward(torch)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     pr.check(pr.pr_tune_save(args.out))
