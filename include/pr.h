@@ -77,8 +77,8 @@ typedef enum {
  *   PLAIN          per-thread fp32 accumulators, fp32 combines (fp64 input: fp64).
  *   COMPENSATED    per-thread fp32 (sum, compensation) pairs, each element added
  *                  with its exact rounding error (TwoSum); pairs combined within
- *                  a block with Neumaier's algorithm in fp32 and across blocks in
- *                  fp64; rounded once.
+ *                  a block with Neumaier's algorithm in fp32; each block's s + c
+ *                  summed across blocks in fp64; rounded once.
  *   FP64_COMBINE   per-thread fp32 accumulators, fp64 warp/block/grid combine. */
 typedef enum {
     PR_PREC_PLAIN = 0, PR_PREC_COMPENSATED = 1, PR_PREC_FP64_COMBINE = 2
@@ -96,7 +96,11 @@ typedef struct {
     int32_t vec_bytes;
 } pr_config;
 
-typedef enum { PR_KIND_REDUCE = 0, PR_KIND_SEGMENTED = 1, PR_KIND_BACKWARD = 2 } pr_kind;
+/* Kernel families with their own configurations: REDUCE (pr_reduce*),
+ * SEGMENTED (pr_segmented_reduce*, and rows that do not fit ROWS), BACKWARD
+ * (pr_reduce_backward), ROWS (pr_reduce_rows when cols is a whole number of
+ * vectors and x is aligned to the vector width; bucketed by rows*cols). */
+typedef enum { PR_KIND_REDUCE = 0, PR_KIND_SEGMENTED = 1, PR_KIND_BACKWARD = 2, PR_KIND_ROWS = 3 } pr_kind;
 
 /* Per-segment state that the product's gradient needs. */
 typedef struct {
@@ -249,7 +253,9 @@ pr_status pr_get_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision pre
 pr_status pr_set_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision precision,
                         int64_t n, const pr_config* cfg);
 /* Time every candidate configuration on the caller's data (x, n; offsets and
- * nseg for PR_KIND_SEGMENTED, else NULL/0) with CUDA events on `stream`, keep
+ * nseg for PR_KIND_SEGMENTED; nseg = rows and n = rows*cols, offsets NULL,
+ * for PR_KIND_ROWS, which is timed with the outputs the differentiation
+ * forward uses; else NULL/0) with CUDA events on `stream`, keep
  * the fastest for n's bucket and return it in *best (may be NULL).  Blocks the
  * host; must not be called during graph capture.  Writes into the library's
  * workspace only. */

@@ -6,8 +6,12 @@
 //            more zeros, 0 everywhere (P_nz = product of the non-zero elements)
 // times grad_out[r].  The work is one streaming write of grad_in (plus a read
 // of x for product rows without zeros): rows are cut into chunks of
-// blockDim*U vectors, each thread writes U vectors of VB bytes; row-uniform
-// values (grad_out, argidx, aux) are read once per chunk.
+// blockDim*U vectors, each thread writes U vectors of VB bytes.  The grid is
+// several times what is resident and chunk t goes to block t mod grid, so the
+// blocks in flight always write one window of neighbouring chunks and the
+// hardware hands the remaining blocks to whichever SMs finish first (no tail of
+// SMs still writing fixed shares).  Row-uniform values (grad_out, argidx, aux)
+// are re-read only when a block's row changes.
 #include "registry.h"
 #include "kernels.cuh"
 
@@ -75,9 +79,14 @@ __global__ void __launch_bounds__(1024) k_backward(BwdArgs a) {
     const F* x = static_cast<const F*>(a.x);
     const int64_t ntiles = a.rows * a.chunks_per_row;
     const int64_t CV = (int64_t)blockDim.x * U;  // vectors per chunk
+    int64_t rc = -1;
+    RowGrad<F> rg{};
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t r = t / a.chunks_per_row, c = t - r * a.chunks_per_row;
-        const RowGrad<F> rg = row_grad<F>(a, r);
+        if (r != rc) {
+            rg = row_grad<F>(a, r);
+            rc = r;
+        }
         const int64_t base = r * a.cols;
         const int64_t mis = (base + a.shift) % VE;
         int64_t head = (VE - mis) % VE;

@@ -28,6 +28,16 @@
 //   order.  Partials are indexed by chunk, not by block, so results are
 //   deterministic for a fixed launch configuration whatever the claim order.
 //
+// k_rows       equal rows of `cols` elements (cols a multiple of the vector
+//   width, x aligned to it): the flattened vectors are split into one run of
+//   whole tiles per block; a block streams its run exactly like k_reduce and
+//   finishes a row each time the run crosses a row end.  The first vectors of
+//   the next row are loaded before that row's block combine, so loads stay in
+//   flight through it.  A row shared by several blocks leaves one partial per
+//   block (the first block's "tail" slot, later blocks' "head" slots); the
+//   last of them to finish (per-row ticket) combines them in block order, so
+//   results are deterministic for a fixed launch configuration.
+//
 // k_combine_parts  one block combining an array of partials in order.
 #pragma once
 #include <type_traits>
@@ -74,6 +84,16 @@ struct SegArgs {
     int out_f64;
     int chunks_per_block;  // chunks (contiguous tile runs) per block
     int dynamic_chunks;    // 1: blocks claim chunks from an atomic counter; 0: chunk c -> block c mod grid
+    Workspace ws;
+};
+
+struct RowArgs {
+    const void* x;       // aligned to the vector width
+    int64_t rows, cols;  // cols > 0, a multiple of the elements per vector
+    void* out;
+    int64_t* argidx;
+    pr_prod_aux* aux;
+    int out_f64;
     Workspace ws;
 };
 
@@ -214,6 +234,115 @@ __global__ void __launch_bounds__(256) k_combine_parts(const char* parts, int co
         q = GR::combine(q, *reinterpret_cast<const G*>(parts + (int64_t)j * kSlot));
     q = block_combine<GR>(q);
     if (threadIdx.x == 0) GR::store(out, 0, q, out_f64 != 0);
+}
+
+// ------------------------------------------------------------------------
+// Row reduction
+// ------------------------------------------------------------------------
+
+template <class T, int U, int VB>
+__global__ void __launch_bounds__(1024) k_rows(RowArgs a) {
+    using Ld = typename T::Ld;
+    using E = typename Ld::E;
+    using Acc = typename T::Acc;
+    using Part = typename T::Part;
+    using GR = GridR<T>;
+    using G = typename GR::Part;
+    constexpr int VE = VB / Ld::ES;
+    const char* xv = static_cast<const char*>(a.x);
+    const bool f64 = a.out_f64 != 0;
+    const int B = blockDim.x;
+    const int64_t cv = a.cols / VE;                 // vectors per row
+    const int64_t nv = a.rows * cv;                 // vectors in all
+    const int64_t TILE = (int64_t)B * U;            // vectors per tile
+    const int64_t ntile = (nv + TILE - 1) / TILE;
+    const int64_t R = (ntile + gridDim.x - 1) / gridDim.x * TILE;  // vectors per block run
+    const int64_t vlo = (int64_t)blockIdx.x * R < nv ? (int64_t)blockIdx.x * R : nv;
+    const int64_t vhi = vlo + R < nv ? vlo + R : nv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    (void)lane;
+    (void)warp;
+    __shared__ int s_fin;
+
+    Words<VB> pre[U];   // this thread's first U vectors of the next row piece
+    bool have = false;
+    for (int64_t v = vlo; v < vhi;) {
+        const int64_t r = v / cv;
+        const int64_t pend = (r + 1) * cv < vhi ? (r + 1) * cv : vhi;
+        Acc acc[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) acc[u] = T::init();
+        int64_t i = v + threadIdx.x;
+        if (have) {
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                E e[VE];
+                Ld::template dec<VB>(pre[u], e);
+                T::add_vec(acc[u], e, (i + (int64_t)u * B) * VE);
+            }
+            i += TILE;
+        }
+        for (; i + (int64_t)(U - 1) * B < pend; i += TILE) {
+            Words<VB> w[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) w[u] = ldv<VB>(xv + (i + (int64_t)u * B) * VB);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                E e[VE];
+                Ld::template dec<VB>(w[u], e);
+                T::add_vec(acc[u], e, (i + (int64_t)u * B) * VE);
+            }
+        }
+        for (; i < pend; i += B) {
+            const Words<VB> w = ldv<VB>(xv + i * VB);
+            E e[VE];
+            Ld::template dec<VB>(w, e);
+            T::add_vec(acc[0], e, i * VE);
+        }
+        // load the next piece's first vectors now, so that they arrive during the combine
+        have = false;
+        if (pend < vhi) {
+            const int64_t nend = pend + cv < vhi ? pend + cv : vhi;
+            const int64_t j = pend + threadIdx.x;
+            if (j + (int64_t)(U - 1) * B < nend) {
+#pragma unroll
+                for (int u = 0; u < U; u++) pre[u] = ldv<VB>(xv + (j + (int64_t)u * B) * VB);
+                have = true;
+            }
+        }
+        // finish this block's piece of row r
+        const Part p = block_combine<T>(fold<T, U>(acc));
+        const int64_t sb = r * a.cols;
+        const int64_t ba = (r * cv) / R, bb = ((r + 1) * cv - 1) / R;
+        if (ba == bb) {
+            if (threadIdx.x == 0) {
+                const G g = GR::up(p);
+                GR::store(a.out, r, g, f64);
+                GR::store_aux(a.argidx, a.aux, r, g, sb);
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                *slot<GR>(v > r * cv ? a.ws.head : a.ws.tail, blockIdx.x) = GR::up(p);
+                __threadfence();
+                const unsigned old = atomicAdd(a.ws.seg_cnt + ba, 1u);
+                s_fin = (old == (unsigned)(bb - ba));
+            }
+            __syncthreads();
+            if (s_fin) {
+                __threadfence();
+                G q = GR::part_init();
+                for (int64_t k = threadIdx.x; k <= bb - ba; k += B)
+                    q = GR::combine(q, ld_cg_any(k == 0 ? slot<GR>(a.ws.tail, ba) : slot<GR>(a.ws.head, ba + k)));
+                q = block_combine<GR>(q);
+                if (threadIdx.x == 0) {
+                    GR::store(a.out, r, q, f64);
+                    GR::store_aux(a.argidx, a.aux, r, q, sb);
+                    a.ws.seg_cnt[ba] = 0u;
+                }
+            }
+        }
+        v = pend;
+    }
 }
 
 // ------------------------------------------------------------------------

@@ -17,6 +17,12 @@ cudaError_t launch_segmented(const SegArgs& a, int grid, int block, cudaStream_t
     return cudaGetLastError();
 }
 
+template <class T, int U, int VB>
+cudaError_t launch_rows(const RowArgs& a, int grid, int block, cudaStream_t st) {
+    k_rows<T, U, VB><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_combine(const char* parts, int count, void* out, int out_f64, cudaStream_t st) {
     k_combine_parts<T><<<1, 256, 0, st>>>(parts, count, out, out_f64);
@@ -34,6 +40,10 @@ void reg_one(uint8_t dtype, uint8_t op, uint8_t prec, uint8_t aux, bool plain, b
         reg_add(KernelKey{K_SEGMENTED, dtype, op, prec, aux, (uint8_t)U, (uint8_t)VB},
                 KernelEntry{reinterpret_cast<const void*>(&k_segmented<T, U, VB>),
                             reinterpret_cast<void*>(&launch_segmented<T, U, VB>)});
+        // equal rows (the differentiation forwards) get the lighter row kernel
+        reg_add(KernelKey{K_ROWS, dtype, op, prec, aux, (uint8_t)U, (uint8_t)VB},
+                KernelEntry{reinterpret_cast<const void*>(&k_rows<T, U, VB>),
+                            reinterpret_cast<void*>(&launch_rows<T, U, VB>)});
     }
 }
 

@@ -10,9 +10,10 @@ namespace pr {
 
 struct ReduceArgs;
 struct SegArgs;
+struct RowArgs;
 struct BwdArgs;
 
-enum Kind : uint8_t { K_REDUCE = 0, K_SEGMENTED = 1, K_BACKWARD = 2, K_COMBINE = 3 };
+enum Kind : uint8_t { K_REDUCE = 0, K_SEGMENTED = 1, K_BACKWARD = 2, K_COMBINE = 3, K_ROWS = 4 };
 enum Aux : uint8_t { AUX_NONE = 0, AUX_ARG = 1, AUX_PROD = 2 };
 
 struct KernelKey {
@@ -22,6 +23,7 @@ struct KernelKey {
 
 using ReduceLaunch = cudaError_t (*)(const ReduceArgs&, int grid, int block, cudaStream_t);
 using SegLaunch = cudaError_t (*)(const SegArgs&, int grid, int block, cudaStream_t);
+using RowLaunch = cudaError_t (*)(const RowArgs&, int grid, int block, cudaStream_t);
 using BwdLaunch = cudaError_t (*)(const BwdArgs&, int grid, int block, cudaStream_t);
 using CombineLaunch = cudaError_t (*)(const char* parts, int count, void* out, int out_f64, cudaStream_t);
 

@@ -173,10 +173,16 @@ struct SumF {
 // Per thread: kLanes independent fp32 (sum, compensation) pairs, element k of
 // a vector going to lane k mod kLanes (independent dependency chains), each
 // element added with TwoSum.  Lanes, threads and warps combine as fp32 pairs
-// with Neumaier's algorithm; only the cross-block combine of block partials
-// runs in fp64
-// (GridPart) -- GB300 issues fp64 adds at ~0.5e12/s, so fp64 inside the block
-// would cost more than the whole HBM stream.  One rounding at the end.
+// with Neumaier's algorithm.  Each block partial s + c then crosses blocks as
+// one fp64 value (GridPart) summed with plain fp64 adds, and the result is
+// rounded once.  fp64 stays out of the block because GB300 issues fp64 adds at
+// ~0.5e12/s (inside the block it would cost more than the whole HBM stream),
+// and the cross-block sum uses single fp64 adds rather than fp64 Neumaier
+// because each fp64 operation of the finishing block's dependent chain costs
+// ~0.5 us there (measured: an fp64 Neumaier tree over 760 block partials took
+// 7 us after the last block's loop, one add per level 2.5 us).  With at most a
+// few thousand partials the fp64 sum errs by < 2^-40 of the sum of |partials|,
+// far inside the compensated bound 2^-24 * sum|x|.
 template <class Ld_>
 struct SumComp {
     using Ld = Ld_;
@@ -184,7 +190,7 @@ struct SumComp {
     static constexpr int kLanes = 4;
     struct Acc { float s[kLanes], c[kLanes]; };
     struct Part { float s, c; };
-    struct GridPart { double s, c; };
+    using GridPart = double;
     static constexpr bool kIdx = false;
     __device__ __forceinline__ static Acc init() {
         Acc a;
@@ -222,11 +228,8 @@ struct SumComp {
         return p;
     }
     __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<SumComp>(p); }
-    // Once an infinity enters, s stays +-inf or NaN and the compensation turns
-    // NaN; the sum is then s itself.
     __device__ __forceinline__ static void grid_store(void* out, int64_t i, const GridPart& g, bool f64) {
-        const double r = isfinite(g.s) ? g.s + g.c : g.s;
-        if (f64) put_f64(out, i, r); else put_f32(out, i, (float)r);
+        if (f64) put_f64(out, i, g); else put_f32(out, i, (float)g);
     }
     __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) {
         grid_store(out, i, to_grid(p), f64);
@@ -235,13 +238,13 @@ struct SumComp {
     __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
         store(out, i, part_init(), f64);
     }
-    __device__ __forceinline__ static GridPart to_grid(const Part& p) { return {(double)p.s, (double)p.c}; }
-    __device__ __forceinline__ static GridPart grid_init() { return {0.0, 0.0}; }
-    __device__ __forceinline__ static GridPart grid_combine(const GridPart& a, const GridPart& b) {
-        const double t = a.s + b.s;
-        const double e = fabs(a.s) >= fabs(b.s) ? (a.s - t) + b.s : (b.s - t) + a.s;
-        return {t, (a.c + b.c) + e};
+    // Once an infinity enters, s stays +-inf or NaN and the compensation turns
+    // NaN; the partial is then s itself.
+    __device__ __forceinline__ static GridPart to_grid(const Part& p) {
+        return isfinite(p.s) ? (double)p.s + (double)p.c : (double)p.s;
     }
+    __device__ __forceinline__ static GridPart grid_init() { return 0.0; }
+    __device__ __forceinline__ static GridPart grid_combine(const GridPart& a, const GridPart& b) { return a + b; }
 };
 
 // fp64 input, fp64 sum.

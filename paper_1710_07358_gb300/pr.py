@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libpr.so")
 DTYPES = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3, "i32": 4, "u32": 5, "i64": 6}
 OPS = {"sum": 0, "prod": 1, "max": 2, "min": 3, "and": 4, "or": 5, "xor": 6}
 PRECISIONS = {"plain": 0, "compensated": 1, "fp64_combine": 2}
-KINDS = {"reduce": 0, "segmented": 1, "backward": 2}
+KINDS = {"reduce": 0, "segmented": 1, "backward": 2, "rows": 3}
 STATUS = {0: "PR_OK", 1: "PR_ERR_INVALID", 2: "PR_ERR_UNSUPPORTED", 3: "PR_ERR_CUDA",
           4: "PR_ERR_TIMEOUT", 5: "PR_ERR_NOMEM"}
 ELEM_SIZE = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "i32": 4, "u32": 4, "i64": 8}
@@ -374,9 +374,16 @@ def set_config(kind: str, dtype: str, op: str, precision: str, n: int, cfg: dict
 
 
 def autotune(kind: str, x, op: str, precision: str = "plain", offsets=None, stream=None) -> dict:
+    """Tune (and keep) the configuration for x's size bucket: kind "reduce"
+    (x 1-D), "segmented" (x 1-D plus offsets) or "rows" (x a contiguous
+    [rows, cols] tensor, timed with the differentiation forward's outputs)."""
     d = dtype_name(x)
     c = pr_config()
     nseg = offsets.numel() - 1 if offsets is not None else 0
+    if kind == "rows":
+        if x.dim() != 2 or not x.is_contiguous():
+            raise ValueError("autotune('rows') needs a contiguous 2-D tensor")
+        nseg = x.shape[0]
     check(pr_autotune(KINDS[kind], _ptr(x), x.numel(), _ptr(offsets), nseg, DTYPES[d], OPS[op],
                       PRECISIONS[precision], _stream(x, stream), ctypes.byref(c)))
     return c.as_dict()

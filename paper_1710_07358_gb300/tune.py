@@ -84,45 +84,15 @@ def tune_backward(torch, rows=64, cols=1 << 20, reps=5):
     return best
 
 
-def tune_rows(torch, rows=64, cols=1 << 20, reps=5):
+def tune_rows(torch, rows=64, cols=1 << 20):
     """Row reductions as autograd runs them (argidx for max/min, product aux for
-    prod): time every segmented-kernel candidate with CUDA events and keep the
-    fastest for the (rows) bucket."""
+    prod), tuned by the library's autotuner for the rows*cols bucket."""
     g = torch.Generator(device="cuda")
     g.manual_seed(2)
     x = torch.randn(rows, cols, generator=g, device="cuda")
     for op in ("sum", "max", "min", "prod"):
-        results = []
-        for block in (128, 256, 512):
-            for bps in (1, 2, 4, 8):
-                if block * bps > 2048:
-                    continue
-                for unroll in (2, 4):
-                    for vb in (16, 32):
-                        cfg = dict(block=block, blocks_per_sm=bps, unroll=unroll, vec_bytes=vb)
-                        pr.set_config("segmented", "f32", op, "plain", rows, cfg)
-
-                        def run():
-                            if op in ("max", "min"):
-                                pr.reduce_rows(x, op, argidx=True)
-                            elif op == "prod":
-                                pr.reduce_rows(x, op, aux=True)
-                            else:
-                                pr.reduce_rows(x, op)
-                        run()
-                        run()
-                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        ts = []
-                        for _ in range(reps):
-                            e0.record()
-                            run()
-                            e1.record()
-                            e1.synchronize()
-                            ts.append(e0.elapsed_time(e1))
-                        results.append((min(ts), cfg))
-        t, cfg = min(results, key=lambda r: r[0])
-        pr.set_config("segmented", "f32", op, "plain", rows, cfg)
-        print("rows %dx%d f32 %s: %.1f us %s" % (rows, cols, op, t * 1e3, cfg), flush=True)
+        cfg = pr.autotune("rows", x, op)
+        print("rows %dx%d f32 %s: %s" % (rows, cols, op, cfg), flush=True)
     del x
 
 
@@ -133,9 +103,15 @@ def main():
     ap.add_argument("--out", default=DEFAULT_PATH)
     ap.add_argument("--sizes", default="20,22,24,26,28,30")
     ap.add_argument("--quick", action="store_true", help="only 2^28 and the segmented workload")
+    ap.add_argument("--only", default="reduce,segmented,rows,backward",
+                    help="comma list of the parts to re-tune; the other entries of the shipped table are kept")
     args = ap.parse_args()
+    parts = set(args.only.split(","))
     sizes = [28] if args.quick else [int(s) for s in args.sizes.split(",")]
+    if "reduce" not in parts:
+        sizes = []
     torch.cuda.set_device(0)
+    pr.lib()                      # loads the shipped table, which the new entries refine
     g = torch.Generator(device="cuda")
     g.manual_seed(1)
     for k in sizes:
@@ -153,19 +129,22 @@ def main():
             print("reduce 2^%d %s sum %s: %s" % (k, dtype, prec, cfg), flush=True)
             del x
         torch.cuda.empty_cache()
-    vals, off = synth.segmented_workload(4096, synth.config_seed(3))
-    xv = torch.from_numpy(vals).cuda()
-    ov = torch.from_numpy(off).cuda()
-    for op in ("sum", "max", "min", "prod"):
-        cfg = pr.autotune("segmented", xv, op, offsets=ov)
-        print("segmented 4096 f32 %s: %s" % (op, cfg), flush=True)
-    for prec in ("compensated", "fp64_combine"):
-        cfg = pr.autotune("segmented", xv, "sum", precision=prec, offsets=ov)
-        print("segmented 4096 f32 sum %s: %s" % (prec, cfg), flush=True)
-    del xv, ov
-    # row reductions of the differentiation workload (64 rows of 2^20)
-    tune_rows(torch)
-    tune_backward(torch)
+    if "segmented" in parts:
+        vals, off = synth.segmented_workload(4096, synth.config_seed(3))
+        xv = torch.from_numpy(vals).cuda()
+        ov = torch.from_numpy(off).cuda()
+        for op in ("sum", "max", "min", "prod"):
+            cfg = pr.autotune("segmented", xv, op, offsets=ov)
+            print("segmented 4096 f32 %s: %s" % (op, cfg), flush=True)
+        for prec in ("compensated", "fp64_combine"):
+            cfg = pr.autotune("segmented", xv, "sum", precision=prec, offsets=ov)
+            print("segmented 4096 f32 sum %s: %s" % (prec, cfg), flush=True)
+        del xv, ov
+    # row reductions and gradients of the differentiation workload (64 rows of 2^20)
+    if "rows" in parts:
+        tune_rows(torch)
+    if "backward" in parts:
+        tune_backward(torch)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     pr.check(pr.pr_tune_save(args.out))
     print("saved", args.out)

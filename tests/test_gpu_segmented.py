@@ -229,10 +229,12 @@ def test_malformed_offsets_raise_device_error_and_recover():
 
 
 @pytest.mark.parametrize("rows,cols,offset", [(10000, 37, 1), (3, (1 << 21) + 5, 3), (1, 1 << 22, 0),
-                                              (64, 4096, 2), (700, 1000, 0)])
+                                              (64, 4096, 2), (700, 1000, 0), (1, 8, 0), (5, 24, 0),
+                                              (64, 1 << 16, 0), (3000, 64, 0), (333, 4104, 0), (2, 1 << 22, 0)])
 def test_row_kernel_shapes(rows, cols, offset):
-    """Many short rows (one item per row) and few long rows split into column
-    chunks combined through per-row tickets, at several alignments."""
+    """Many short rows (many per block) and few long rows split across blocks
+    and combined through per-row tickets.  Aligned rows that are a whole
+    number of vectors take the row kernel, the others the segmented kernel."""
     x = synth.normal_f32(rows * cols, rows + cols)
     t = to_device(x, "f32", offset).view(rows, cols)
     off = np.arange(rows + 1, dtype=np.int64) * cols
@@ -256,3 +258,67 @@ def test_row_kernel_shapes(rows, cols, offset):
         assert abs(p_nz[r] - wp) <= prod_rel_bound(cols, "f32") * abs(wp)
         want = oracle.reduce(seg, "f32", "prod")
         assert abs(vals[r] - want) <= prod_rel_bound(cols, "f32") * abs(want)
+
+
+ROW_PAIRS = [("bf16", "sum"), ("f16", "max"), ("f64", "sum"), ("f64", "prod"), ("f64", "min"), ("i32", "sum"),
+             ("i32", "max"), ("u32", "xor"), ("i64", "sum"), ("i64", "min")]
+
+
+@pytest.mark.parametrize("dtype,op", ROW_PAIRS)
+def test_row_kernel_dtypes(dtype, op):
+    rows, cols = 37, 3 * 4096
+    x = gen_vals(dtype, op, rows * cols, 31)
+    t = to_device(x, dtype).view(rows, cols)
+    off = np.arange(rows + 1, dtype=np.int64) * cols
+    od = pr.out_dtype_name(dtype, op)
+    if op in ("max", "min"):
+        out, ai = pr.reduce_rows(t, op, argidx=True)
+        check_segments(x, off, dtype, op, values_of(out, od), argidx=ai.cpu().numpy())
+    else:
+        check_segments(x, off, dtype, op, values_of(pr.reduce_rows(t, op), od))
+
+
+@pytest.mark.parametrize("precision", ["fp64_combine", "compensated"])
+def test_row_kernel_precision_modes(precision):
+    rows, cols = 9, 1 << 18
+    x, _, _ = synth.ill_conditioned_f32(rows * cols, 32)
+    t = to_device(x, "f32").view(rows, cols)
+    off = np.arange(rows + 1, dtype=np.int64) * cols
+    check_segments(x, off, "f32", "sum", values_of(pr.reduce_rows(t, "sum", precision=precision), "f32"),
+                   precision=precision)
+
+
+def test_row_kernel_every_config_variant():
+    import torch
+    rows, cols = 7, 40000
+    x = synth.normal_f32(rows * cols, 33)
+    xp = synth.uniform_f32(rows * cols, 34, 1 - 2.0 ** -7, 1 + 2.0 ** -7)
+    xp[5 * cols + 123] = 0.0
+    t = to_device(x, "f32").view(rows, cols)
+    tp = to_device(xp, "f32").view(rows, cols)
+    off = np.arange(rows + 1, dtype=np.int64) * cols
+    n = rows * cols
+    old = {op: pr.get_config("rows", "f32", op, "plain", n) for op in ("sum", "max", "prod")}
+    ref = None
+    try:
+        for block in (128, 256, 512, 1024):
+            for unroll in (2, 4):
+                for vb in (16, 32):
+                    cfg = dict(block=block, blocks_per_sm=2, unroll=unroll, vec_bytes=vb)
+                    for op in old:
+                        pr.set_config("rows", "f32", op, "plain", n, cfg)
+                    out, ai = pr.reduce_rows(t, "max", argidx=True)
+                    check_segments(x, off, "f32", "max", values_of(out, "f32"), argidx=ai.cpu().numpy())
+                    s1 = pr.reduce_rows(t, "sum")
+                    check_segments(x, off, "f32", "sum", values_of(s1, "f32"))
+                    assert torch.equal(pr.reduce_rows(t, "sum").view(torch.int32), s1.view(torch.int32))
+                    out, ax = pr.reduce_rows(tp, "prod", aux=True)
+                    p_nz, zc, zi = (v.cpu().numpy() for v in pr.prod_aux_fields(ax))
+                    for r in range(rows):
+                        seg = xp[r * cols:(r + 1) * cols]
+                        wp, wz, wi = oracle.prod_aux(seg, "f32")
+                        assert zc[r] == wz and zi[r] == wi
+                        assert abs(p_nz[r] - wp) <= prod_rel_bound(cols, "f32") * abs(wp)
+    finally:
+        for op, c in old.items():
+            pr.set_config("rows", "f32", op, "plain", n, c)
