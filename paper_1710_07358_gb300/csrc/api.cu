@@ -221,6 +221,31 @@ static pr_status occupancy(const void* fn, int block, int* bps) {
     return PR_OK;
 }
 
+static std::map<const void*, int> g_maxthr;
+
+// The configuration with its block size clamped to the kernel's compiled limit
+// (a trait with a large per-thread state compiles for at most 512 threads).
+static pr_config fit_block(const KernelEntry* e, pr_config c) {
+    int mt = 1024;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_maxthr.find(e->fn);
+        if (it != g_maxthr.end()) {
+            mt = it->second;
+        } else {
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, e->fn) == cudaSuccess) {
+                mt = fa.maxThreadsPerBlock;
+                g_maxthr.emplace(e->fn, mt);
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
+    if (c.block > mt) c.block = mt / 32 * 32;
+    return c;
+}
+
 // Persistent grid: SMs x blocks-per-SM (clamped to what is resident at once).
 static pr_status persistent_grid(const KernelEntry* e, const pr_config& c, int sms, int gmax, int* grid) {
     int occ = 0;
@@ -238,11 +263,12 @@ static pr_status persistent_grid(const KernelEntry* e, const pr_config& c, int s
 // ------------------------------------------------------------------------
 
 static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int prec, bool out_f64, void* out,
-                            void* part_out, cudaStream_t st, const pr_config& c, int aux = AUX_NONE,
+                            void* part_out, cudaStream_t st, const pr_config& cfg, int aux = AUX_NONE,
                             int64_t* argidx = nullptr) {
     const KernelEntry* e = reg_find(KernelKey{K_REDUCE, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec, (uint8_t)aux,
-                                              (uint8_t)c.unroll, (uint8_t)c.vec_bytes});
+                                              (uint8_t)cfg.unroll, (uint8_t)cfg.vec_bytes});
     if (!e) return fail(PR_ERR_UNSUPPORTED, "no reduce kernel for dtype %d op %d precision %d", dtype, op, prec);
+    const pr_config c = fit_block(e, cfg);
     DevInfo di;
     pr_status s = device_info(&di, nullptr);
     if (s != PR_OK) return s;
@@ -312,14 +338,15 @@ static pr_status run_segmented(const void* x, const int64_t* off, int64_t cols, 
 // Row kernel for equal rows; PR_ERR_UNSUPPORTED (nothing enqueued, no message
 // kept) when the shape or alignment needs the general segmented kernel.
 static pr_status run_rows(const void* x, int64_t rows, int64_t cols, int dtype, int op, int prec, int aux, void* out,
-                          int64_t* argidx, pr_prod_aux* paux, cudaStream_t st, const pr_config& c) {
+                          int64_t* argidx, pr_prod_aux* paux, cudaStream_t st, const pr_config& cfg) {
     const int es = elem_size(dtype);
-    const int64_t ve = c.vec_bytes / es;
-    if (rows < 1 || cols < 1 || cols % ve != 0 || reinterpret_cast<uintptr_t>(x) % (uintptr_t)c.vec_bytes != 0)
+    const int64_t ve = cfg.vec_bytes / es;
+    if (rows < 1 || cols < 1 || cols % ve != 0 || reinterpret_cast<uintptr_t>(x) % (uintptr_t)cfg.vec_bytes != 0)
         return PR_ERR_UNSUPPORTED;
     const KernelEntry* e = reg_find(KernelKey{K_ROWS, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec, (uint8_t)aux,
-                                              (uint8_t)c.unroll, (uint8_t)c.vec_bytes});
+                                              (uint8_t)cfg.unroll, (uint8_t)cfg.vec_bytes});
     if (!e) return PR_ERR_UNSUPPORTED;
+    const pr_config c = fit_block(e, cfg);
     DevInfo di;
     pr_status s = device_info(&di, nullptr);
     if (s != PR_OK) return s;

@@ -138,6 +138,18 @@ struct GridR<T, std::void_t<typename T::GridPart>> {
     __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
 };
 
+// Largest block a trait's kernels are compiled for (a trait with a large
+// per-thread state declares kMaxBlock to get more registers per thread); the
+// host clamps launch configurations to it.
+template <class T, class = void>
+struct MaxBlock {
+    static constexpr int value = 1024;
+};
+template <class T>
+struct MaxBlock<T, std::void_t<decltype(T::kMaxBlock)>> {
+    static constexpr int value = T::kMaxBlock;
+};
+
 template <class T>
 __device__ __forceinline__ typename T::Part* slot(char* base, int64_t i) {
     return reinterpret_cast<typename T::Part*>(base + i * kSlot);
@@ -157,7 +169,7 @@ __device__ __forceinline__ typename T::Part fold(typename T::Acc (&acc)[U]) {
 // ------------------------------------------------------------------------
 
 template <class T, int U, int VB>
-__global__ void __launch_bounds__(1024) k_reduce(ReduceArgs a) {
+__global__ void __launch_bounds__(MaxBlock<T>::value) k_reduce(ReduceArgs a) {
     using Ld = typename T::Ld;
     using In = typename Ld::In;
     using E = typename Ld::E;
@@ -241,7 +253,7 @@ __global__ void __launch_bounds__(256) k_combine_parts(const char* parts, int co
 // ------------------------------------------------------------------------
 
 template <class T, int U, int VB>
-__global__ void __launch_bounds__(1024) k_rows(RowArgs a) {
+__global__ void __launch_bounds__(MaxBlock<T>::value) k_rows(RowArgs a) {
     using Ld = typename T::Ld;
     using E = typename Ld::E;
     using Acc = typename T::Acc;

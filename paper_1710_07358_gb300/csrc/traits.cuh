@@ -554,23 +554,59 @@ struct ArgExt {
     }
 };
 
-// Float extremum plus first index, for f32 (and bf16 / f16 widened to f32):
-// a vector's extremum is taken with max.NaN / min.NaN (one instruction per
-// element); only when it can replace the running best is the vector searched
-// for the first element with the same key.  Same result as ArgExt<KeyF32>.
+// Float extremum plus first index, for f32 (and bf16 / f16 widened to f32).
+// A thread sees only a few dozen vectors per accumulator, so its running best
+// changes often, and in a warp some lane almost always changes: a search of
+// the vector on every change would run on nearly every vector.  Instead each
+// accumulator keeps the best VECTOR so far: its elements, its first index and
+// its extremum's key, updated with selects (no branch); the element index
+// inside it is found once, in to_part.  A vector's extremum is max.NaN /
+// min.NaN over its elements (a NaN yields the canonical NaN, whose raw key is
+// already extreme for max; for min the key is shifted by one so that it wraps
+// to 0).  Vectors reach add_vec in increasing index order per accumulator, so
+// only a strictly better key replaces the best vector.  Scalars (head, tail and
+// masked elements), which may arrive out of order, keep their own (key, index)
+// best with the full comparison.  Same result as ArgExt<KeyF32>.
 template <class Ld_, int OutK, bool MX>
 struct ArgExtF {
     using Ld = Ld_;
     using E = float;
     using Key = KeyF32<Ld_, OutK>;
     using Base = ArgExt<Key, MX>;
-    using Acc = typename Base::Acc;
-    using Part = Acc;
+    using Part = typename Base::Part;
     static constexpr bool kIdx = true;
-    __device__ __forceinline__ static Acc init() { return Base::init(); }
-    __device__ __forceinline__ static void add(Acc& a, E v, int64_t i) { Base::add(a, v, i); }
+    static constexpr int kMaxN = 32 / Ld::ES;     // elements of the widest vector
+    static constexpr int kMaxBlock = 512;         // the saved vectors need up to 128 registers
+    struct Acc {
+        float w[kMaxN];   // best vector's elements (the first n are valid)
+        uint32_t kv;      // its extremum's key, shifted by one for min
+        int n;
+        int64_t iv;       // its first element's index (kNone: none yet)
+        uint32_t ks;      // best scalar: key and index
+        int64_t is;
+    };
+    __device__ __forceinline__ static uint32_t raw_key(float v) {
+        const uint32_t b = __float_as_uint(v);
+        return b ^ ((uint32_t)((int32_t)b >> 31) | 0x80000000u);
+    }
+    __device__ __forceinline__ static Acc init() {
+        Acc a;
+#pragma unroll
+        for (int k = 0; k < kMaxN; k++) a.w[k] = 0.f;
+        a.kv = MX ? 0u : 0xffffffffu;   // below (above) every key a vector can have
+        a.n = 0;
+        a.iv = Base::kNone;
+        a.ks = Key::ident(MX);
+        a.is = Base::kNone;
+        return a;
+    }
+    __device__ __forceinline__ static void add(Acc& a, E v, int64_t i) {
+        const uint32_t k = Key::key(v, MX);
+        if (Base::better(k, i, a.ks, a.is)) { a.ks = k; a.is = i; }
+    }
     template <int N>
     __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[N], int64_t i0) {
+        static_assert(N <= kMaxN, "vector wider than the saved copy");
         float t[N];
 #pragma unroll
         for (int k = 0; k < N; k++) t[k] = e[k];
@@ -578,20 +614,29 @@ struct ArgExtF {
         for (int s = 1; s < N; s <<= 1)
 #pragma unroll
             for (int k = 0; k + s < N; k += 2 * s) t[k] = MaxMinF<Ld_, OutK, MX>::f(t[k], t[k + s]);
-        const uint32_t km = Key::key(t[0], MX);
-        // i0 bounds the vector's indices from below: if even that cannot win, nothing in it can
-        if (Base::better(km, i0, a.key, a.idx)) {
-            int kk = N - 1;
+        const uint32_t km = MX ? raw_key(t[0]) : raw_key(t[0]) + 1u;
+        const bool up = MX ? km > a.kv : km < a.kv;
+        a.kv = up ? km : a.kv;
+        a.iv = up ? i0 : a.iv;
 #pragma unroll
-            for (int k = N - 1; k >= 0; k--)
-                if (Key::key(e[k], MX) == km) kk = k;
-            if (Base::better(km, i0 + kk, a.key, a.idx)) { a.key = km; a.idx = i0 + kk; }
-        }
+        for (int k = 0; k < N; k++) a.w[k] = up ? e[k] : a.w[k];
+        a.n = N;
     }
-    __device__ __forceinline__ static Part to_part(const Acc& a) { return a; }
+    __device__ __forceinline__ static Part to_part(const Acc& a) {
+        Part p{a.ks, a.is};
+        if (a.iv != Base::kNone) {
+            const uint32_t kv = MX ? a.kv : (a.kv == 0u ? 0u : a.kv - 1u);   // as Key::key
+            int kk = kMaxN - 1;
+#pragma unroll
+            for (int k = kMaxN - 1; k >= 0; k--)
+                if (k < a.n && Key::key(a.w[k], MX) == kv) kk = k;
+            p = Base::combine(p, Part{kv, a.iv + kk});
+        }
+        return p;
+    }
     __device__ __forceinline__ static Part part_init() { return Base::part_init(); }
     __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return Base::combine(a, b); }
-    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<ArgExtF>(p); }
+    __device__ __forceinline__ static Part warp_reduce(Part p) { return Base::warp_reduce(p); }
     __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) { Base::store(out, i, p, f64); }
     __device__ __forceinline__ static void store_aux(int64_t* argidx, pr_prod_aux* aux, int64_t i, const Part& p,
                                                      int64_t seg_begin) {
@@ -760,27 +805,28 @@ template <class Base>
 struct ProdAux {
     using Ld = typename Base::Ld;
     using E = typename Ld::E;
-    // zsv: xor of the zeros' sign words (bit 31 is the sign of a +-0)
-    struct Acc { typename Base::Acc p; int64_t zi; uint32_t zc; uint32_t zsv; };
-    struct Part { typename Base::Part p; int64_t zc; int64_t zi; uint32_t zsign; uint32_t pad_; };
+    // sx: xor of every element's sign word (bit 31 is the sign of the element;
+    // with a zero present it is the sign of the whole product)
+    struct Acc { typename Base::Acc p; int64_t zi; uint32_t zc; uint32_t sx; };
+    struct Part { typename Base::Part p; int64_t zc; int64_t zi; uint32_t sall; uint32_t pad_; };
     static constexpr bool kIdx = true;
     __device__ __forceinline__ static uint32_t sign_word(E v) {
         if constexpr (sizeof(E) == 8) return (uint32_t)((uint64_t)__double_as_longlong(v) >> 32);
         else return __float_as_uint(v);
     }
-    __device__ __forceinline__ static Acc init() { Acc a; a.p = Base::init(); a.zi = INT64_MAX; a.zc = 0; a.zsv = 0; return a; }
+    __device__ __forceinline__ static Acc init() { Acc a; a.p = Base::init(); a.zi = INT64_MAX; a.zc = 0; a.sx = 0; return a; }
     __device__ __forceinline__ static void add(Acc& a, E v, int64_t i) {
+        a.sx ^= sign_word(v);
         if (v == (E)0) {
             a.zc += 1;
             a.zi = i < a.zi ? i : a.zi;
-            a.zsv ^= sign_word(v);
         } else {
             Base::add(a.p, v, i);
         }
     }
     // Zeros are replaced by 1 for the product (so the vector multiplies as a
-    // tree in the base trait); the zero count, first zero and zero signs come
-    // from a bit mask without per-element branches.
+    // tree in the base trait); the zero count and first zero come from a bit
+    // mask, the sign from an xor of all sign words: no per-element branch.
     template <int K>
     __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[K], int64_t i0) {
         static_assert(K <= 32, "zero mask is one word");
@@ -791,18 +837,18 @@ struct ProdAux {
             const bool z = e[k] == (E)0;
             t[k] = z ? (E)1 : e[k];
             mask |= (uint32_t)z << k;
-            sx ^= z ? sign_word(e[k]) : 0u;
+            sx ^= sign_word(e[k]);
         }
         Base::add_vec(a.p, t, i0);
         a.zc += __popc(mask);
-        a.zsv ^= sx;
+        a.sx ^= sx;
         if (mask) {
             const int64_t i = i0 + __ffs(mask) - 1;
             a.zi = i < a.zi ? i : a.zi;
         }
     }
     __device__ __forceinline__ static Part to_part(const Acc& a) {
-        Part r; r.p = Base::to_part(a.p); r.zc = a.zc; r.zi = a.zi; r.zsign = a.zsv >> 31; r.pad_ = 0; return r;
+        Part r; r.p = Base::to_part(a.p); r.zc = a.zc; r.zi = a.zi; r.sall = a.sx >> 31; r.pad_ = 0; return r;
     }
     __device__ __forceinline__ static Part part_init() { return to_part(init()); }
     __device__ __forceinline__ static Part combine(const Part& a, const Part& b) {
@@ -810,14 +856,16 @@ struct ProdAux {
         r.p = Base::combine(a.p, b.p);
         r.zc = a.zc + b.zc;
         r.zi = a.zi < b.zi ? a.zi : b.zi;
-        r.zsign = a.zsign ^ b.zsign;
+        r.sall = a.sall ^ b.sall;
         r.pad_ = 0;
         return r;
     }
     __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<ProdAux>(p); }
+    // With a zero the product is a zero whose sign is the xor of all signs,
+    // unless the non-zero part is infinite or NaN (then NaN, as inf * 0).
     __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) {
         const double pnz = Base::value(p.p);
-        const double v = p.zc > 0 ? pnz * (p.zsign ? -0.0 : 0.0) : pnz;
+        const double v = p.zc > 0 ? (isfinite(pnz) ? (p.sall ? -0.0 : 0.0) : pnz * 0.0) : pnz;
         if (Base::kOutF64) put_f64(out, i, v); else put_f32(out, i, (float)v);
     }
     __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux* aux, int64_t i, const Part& p,
