@@ -295,11 +295,12 @@ static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int pre
 // Segmented work split, measured on GB300: every chunk switch or segment
 // boundary costs a block a combine (~3 us with its loads drained), so with few
 // segments per block one static chunk per block is fastest (64 rows of 2^20:
-// 49 us vs 58 us with 4 chunks), while many uneven segments want several
-// chunks claimed dynamically (4096 log-uniform segments: 203 us vs 220 us).
+// 49 us vs 58 us with 4 chunks), while many uneven segments want a few chunks
+// claimed dynamically (4096 log-uniform segments: 220 us with one static chunk
+// per block, 201-204 us with 8 dynamic chunks per block, 196-198 us with 2).
 static void seg_split(int64_t nseg, int grid, int gmax, int* chunks_per_block, int* dynamic) {
     if (nseg > 2 * (int64_t)grid) {
-        int c = 8;
+        int c = 2;
         while (c > 1 && (int64_t)c * grid > gmax) c >>= 1;
         *chunks_per_block = c;
         *dynamic = 1;

@@ -15,9 +15,10 @@
 //
 // k_segmented  many reductions (segments of a CSR offsets array, or equal rows)
 //   in one launch.  The element range [offsets[0], offsets[nseg]) is cut into
-//   tiles of blockDim*U*VB bytes, and runs of tiles form chunks (about four
-//   per block) that blocks claim dynamically from an atomic counter, so that
-//   blocks delayed by many segment boundaries do not hold up the launch.
+//   tiles of blockDim*U*VB bytes, and runs of tiles form chunks.  With many
+//   segments per block there are two chunks per block, claimed dynamically
+//   from an atomic counter so that blocks delayed by many segment boundaries
+//   do not hold up the launch; with few, one static chunk per block.
 //   Inside a tile that lies in one segment the block streams exactly like
 //   k_reduce; a tile containing segment boundaries emits the finished
 //   segment, reduces the segments that lie wholly inside the tile (short ones
@@ -547,13 +548,15 @@ __global__ void __launch_bounds__(512) k_segmented(SegArgs a) {
                 s_fin = (old == (unsigned)(bb - ba));
             }
             __syncthreads();
-            if (s_fin && warp == 0) {
+            if (s_fin) {
+                // the whole block combines the segment's chunk partials (a
+                // segment can span every chunk of the launch)
                 __threadfence();
                 G q = GR::part_init();
-                for (int64_t k = lane; k <= bb - ba; k += 32)
+                for (int64_t k = threadIdx.x; k <= bb - ba; k += B)
                     q = GR::combine(q, ld_cg_any(k == 0 ? slot<GR>(a.ws.tail, ba) : slot<GR>(a.ws.head, ba + k)));
-                q = GR::warp_reduce(q);
-                if (lane == 0) {
+                q = block_combine<GR>(q);
+                if (threadIdx.x == 0) {
                     GR::store(a.out, s, q, f64);
                     GR::store_aux(a.argidx, a.aux, s, q, sb);
                     a.ws.seg_cnt[ba] = 0u;
