@@ -100,8 +100,20 @@ __global__ void __launch_bounds__(1024) k_backward(BwdArgs a) {
             if (v < nvec) {
                 const int64_t c0 = head + v * VE;
                 F vals[VE];
+                // row-uniform branches: the broadcast and one-hot rows cost no
+                // per-element arithmetic beyond one compare
+                if (rg.div) {
 #pragma unroll
-                for (int k = 0; k < VE; k++) vals[k] = elem_grad(rg, xrow, c0 + k);
+                    for (int k = 0; k < VE; k++) vals[k] = rg.gv / xrow[c0 + k];
+                } else if (rg.hot == -2) {
+#pragma unroll
+                    for (int k = 0; k < VE; k++) vals[k] = rg.gv;
+                } else {
+                    const int64_t h = rg.hot - c0;
+                    const int hk = (h >= 0 && h < VE) ? (int)h : -1;
+#pragma unroll
+                    for (int k = 0; k < VE; k++) vals[k] = hk == k ? rg.gv : (F)0;
+                }
                 st_vec<F, VB>(grow + c0, vals);
             }
         }
