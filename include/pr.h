@@ -99,8 +99,13 @@ typedef struct {
 /* Kernel families with their own configurations: REDUCE (pr_reduce*),
  * SEGMENTED (pr_segmented_reduce*, and rows that do not fit ROWS), BACKWARD
  * (pr_reduce_backward), ROWS (pr_reduce_rows when cols is a whole number of
- * vectors and x is aligned to the vector width; bucketed by rows*cols). */
-typedef enum { PR_KIND_REDUCE = 0, PR_KIND_SEGMENTED = 1, PR_KIND_BACKWARD = 2, PR_KIND_ROWS = 3 } pr_kind;
+ * vectors and x is aligned to the vector width; bucketed by rows*cols), AXIS
+ * (pr_reduce_axis with inner > 1; bucketed by outer*n*inner: block and
+ * blocks_per_sm size the warps in flight, unroll the rows in flight per lane,
+ * vec_bytes the column vectors when a row is a whole number of them). */
+typedef enum {
+    PR_KIND_REDUCE = 0, PR_KIND_SEGMENTED = 1, PR_KIND_BACKWARD = 2, PR_KIND_ROWS = 3, PR_KIND_AXIS = 4
+} pr_kind;
 
 /* Per-segment state that the product's gradient needs. */
 typedef struct {
@@ -170,6 +175,24 @@ pr_status pr_reduce_rows(const void* x, int64_t rows, int64_t cols, pr_dtype dty
                          pr_precision precision, void* out, int64_t* argidx,
                          pr_prod_aux* aux, pr_stream_t stream);
 
+/* Reduction along one axis of a contiguous row-major [outer, n, inner] array:
+ *   out[p*inner + q] = reduction over i in [0, n) of x[(p*n + i)*inner + q]
+ * for p < outer, q < inner (Section 1.1 applied to every column of every
+ * [n, inner] slab).  Any single axis of a contiguous tensor of shape S reduces
+ * with outer = S[0]*...*S[d-1], n = S[d], inner = S[d+1]*...; inner == 1 is
+ * pr_reduce_rows.  Optional outputs as in pr_segmented_reduce_aux, one per
+ * output element: argidx (MAX/MIN) is the index i along the axis of the first
+ * extremum; aux (PROD, F32/F64) the product state.  n == 0 gives identities.
+ * outer, n, inner >= 0 (PR_ERR_INVALID otherwise or when outer*n*inner
+ * exceeds 2^62).  x is read, out (outer*inner elements of pr_out_dtype) written;
+ * all device memory of the caller.  Shapes with many rows per output use a
+ * per-stream partials buffer grown on first use (outside graph capture:
+ * PR_ERR_INVALID if a captured call would need to grow it).  The result is
+ * deterministic for a fixed configuration. */
+pr_status pr_reduce_axis(const void* x, int64_t outer, int64_t n, int64_t inner, pr_dtype dtype,
+                         pr_op op, pr_precision precision, void* out, int64_t* argidx,
+                         pr_prod_aux* aux, pr_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Differentiation of a row reduction (F32 and F64)                         */
 /* ---------------------------------------------------------------------- */
@@ -186,6 +209,15 @@ pr_status pr_reduce_rows(const void* x, int64_t rows, int64_t cols, pr_dtype dty
 pr_status pr_reduce_backward(pr_op op, pr_dtype dtype, const void* x, int64_t rows, int64_t cols,
                              const void* grad_out, const int64_t* argidx,
                              const pr_prod_aux* aux, void* grad_in, pr_stream_t stream);
+
+/* Gradient of pr_reduce_axis: grad_in[p, i, q] = d out[p, q] / d x[p, i, q] *
+ * grad_out[p, q], with the rules of pr_reduce_backward per output element
+ * (argidx / aux as written by pr_reduce_axis).  grad_in: [outer, n, inner];
+ * grad_out: [outer, inner]; x read only for PROD.  inner == 1 is
+ * pr_reduce_backward.  Status codes as for pr_reduce_backward. */
+pr_status pr_reduce_axis_backward(pr_op op, pr_dtype dtype, const void* x, int64_t outer, int64_t n,
+                                  int64_t inner, const void* grad_out, const int64_t* argidx,
+                                  const pr_prod_aux* aux, void* grad_in, pr_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
 /* End to end from host memory                                              */

@@ -252,6 +252,28 @@ def segmented_argext(x, offsets, dtype: str, op: str):
 
 
 # ---------------------------------------------------------------------------
+# Reduction along one axis of a contiguous [outer, n, inner] array
+# ---------------------------------------------------------------------------
+
+def axis_slices(x, dtype: str, outer: int, n: int, inner: int):
+    """The outer*inner columns x[p, :, q] as contiguous arrays, output order (p, q)."""
+    a = _arr(x, dtype).reshape(outer, n, inner)
+    for p in range(outer):
+        for q in range(inner):
+            yield np.ascontiguousarray(a[p, :, q])
+
+
+def axis(x, dtype: str, op: str, outer: int, n: int, inner: int):
+    """out[p*inner + q] = reduce(x[p, :, q]) (the identity when n == 0)."""
+    return [reduce(c, dtype, op) if n else identity(dtype, op) for c in axis_slices(x, dtype, outer, n, inner)]
+
+
+def axis_argext(x, dtype: str, op: str, outer: int, n: int, inner: int):
+    """Per output (extremum, first index i along the axis)."""
+    return [argext(c, dtype, op) for c in axis_slices(x, dtype, outer, n, inner)]
+
+
+# ---------------------------------------------------------------------------
 # Gradients of a reduction along the last dimension of a [rows, cols] array
 # ---------------------------------------------------------------------------
 

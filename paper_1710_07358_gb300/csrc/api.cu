@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/pr.h"
+#include "axis.cuh"
 #include "kernels.cuh"
 #include "registry.h"
 
@@ -103,6 +104,8 @@ struct WsRec {
     Workspace ws;
     void* base;
     size_t bytes;
+    void* axis = nullptr;    // axis-reduction partials, grown on demand
+    size_t axis_bytes = 0;
 };
 static std::map<std::pair<int, cudaStream_t>, WsRec> g_ws;
 
@@ -187,6 +190,7 @@ static pr_config default_cfg(int kind, int dtype, int op, int prec) {
     (void)dtype; (void)op; (void)prec;
     if (kind == PR_KIND_BACKWARD) return pr_config{512, 4, 4, 16};
     if (kind == PR_KIND_ROWS) return pr_config{512, 2, 2, 32};
+    if (kind == PR_KIND_AXIS) return pr_config{256, 4, 2, 32};
     if (kind == PR_KIND_SEGMENTED) return pr_config{256, 2, 4, 32};
     return pr_config{512, 2, 2, 32};
 }
@@ -397,6 +401,133 @@ static pr_status run_backward(int op, int dtype, const void* x, int64_t rows, in
     return PR_OK;
 }
 
+// Axis partials for (device, stream): at least `bytes`, grown outside graph
+// capture (the first call with a shape needing more must not be captured).
+static pr_status axis_scratch(cudaStream_t st, size_t bytes, char** out) {
+    Workspace ws;
+    pr_status s = get_ws(st, &ws);
+    if (s != PR_OK) return s;
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    WsRec& w = g_ws[std::make_pair(dev, st)];
+    if (w.axis_bytes < bytes) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        PR_CUDA(cudaStreamIsCapturing(st, &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(PR_ERR_INVALID, "axis partials need %zu bytes: run this shape once before graph capture", bytes);
+        PR_CUDA(cudaStreamSynchronize(st));
+        if (w.axis) cudaFree(w.axis);
+        w.axis = nullptr;
+        w.axis_bytes = 0;
+        size_t grow = bytes < ((size_t)1 << 20) ? ((size_t)1 << 20) : bytes;
+        if (cudaMalloc(&w.axis, grow) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PR_ERR_NOMEM, "axis partials: allocation of %zu bytes failed", grow);
+        }
+        w.axis_bytes = grow;
+    }
+    *out = static_cast<char*>(w.axis);
+    return PR_OK;
+}
+
+// Reduction of the middle axis of [outer, n, inner] (inner > 1, outer > 0).
+// The launch: warps per (slab, column group) times row splits, enough warps
+// for about two waves of the resident ones; splits > 1 add a finishing pass.
+static pr_status run_axis(const void* x, int64_t outer, int64_t n, int64_t inner, int dtype, int op, int prec,
+                          int aux, void* out, int64_t* argidx, pr_prod_aux* paux, cudaStream_t st,
+                          const pr_config& cfg) {
+    const int es = elem_size(dtype);
+    DevInfo di;
+    pr_status s = device_info(&di, nullptr);
+    if (s != PR_OK) return s;
+    AxisArgs a{x, outer, n, inner, 0, 1, 0, 1, 0, out, argidx, paux, 0, nullptr};
+    if (n == 0) {
+        const KernelEntry* e = reg_find(KernelKey{K_AXIS_EMPTY, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec,
+                                                  (uint8_t)aux, 0, 0});
+        if (!e) return fail(PR_ERR_UNSUPPORTED, "no axis kernel for dtype %d op %d precision %d", dtype, op, prec);
+        const int64_t nout = outer * inner;
+        int grid = (int)((nout + 255) / 256 < 4096 ? (nout + 255) / 256 : 4096);
+        cudaError_t err = reinterpret_cast<AxisLaunch>(e->launch)(a, grid, 256, st);
+        if (err != cudaSuccess) return fail(PR_ERR_CUDA, "axis launch: %s", cudaGetErrorString(err));
+        return PR_OK;
+    }
+    // vector columns when a row is a whole number of aligned vectors, else one element per lane
+    int vb = cfg.vec_bytes;
+    if (inner % (vb / es) != 0 || reinterpret_cast<uintptr_t>(x) % (uintptr_t)vb != 0) vb = 0;
+    const KernelEntry* e = reg_find(KernelKey{K_AXIS, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec, (uint8_t)aux,
+                                              (uint8_t)cfg.unroll, (uint8_t)vb});
+    if (!e) return fail(PR_ERR_UNSUPPORTED, "no axis kernel for dtype %d op %d precision %d", dtype, op, prec);
+    const pr_config c = fit_block(e, cfg);
+    int occ = 0;
+    s = occupancy(e->fn, c.block, &occ);
+    if (s != PR_OK) return s;
+    if (occ < 1) return fail(PR_ERR_UNSUPPORTED, "axis kernel cannot run with %d threads per block", c.block);
+    const int bps = c.blocks_per_sm < occ ? c.blocks_per_sm : occ;
+    const int ve = vb ? vb / es : 1;
+    a.qv = inner / ve;
+    int bx = 1;
+    while (bx < 32 && bx < a.qv) bx <<= 1;
+    a.bx = bx;
+    a.groups = (a.qv + bx - 1) / bx;
+    const int64_t tiles = outer * a.groups;
+    const int64_t want = (int64_t)di.sms * bps * (c.block / 32) * 2;   // two waves of resident warps
+    const int64_t ry = 32 / bx;
+    int64_t max_split = n / (ry * c.unroll * 4);                        // >= 4 unrolled steps per warp
+    if (max_split < 1) max_split = 1;
+    if (max_split > 1024) max_split = 1024;
+    int64_t splits = (want + tiles - 1) / tiles;
+    if (splits > max_split) splits = max_split;
+    if (splits < 1) splits = 1;
+    a.rows_per_split = (n + splits - 1) / splits;
+    a.splits = (n + a.rows_per_split - 1) / a.rows_per_split;
+    if (a.splits > 1) {
+        char* sc = nullptr;
+        s = axis_scratch(st, (size_t)(outer * inner) * (size_t)a.splits * (size_t)e->part_bytes, &sc);
+        if (s != PR_OK) return s;
+        a.scratch = sc;
+    }
+    const int64_t warps = tiles * a.splits;
+    const int wpb = c.block / 32;
+    const int64_t grid = (warps + wpb - 1) / wpb;
+    if (grid > 0x7fffffff) return fail(PR_ERR_INVALID, "axis reduction too large for one launch");
+    cudaError_t err = reinterpret_cast<AxisLaunch>(e->launch)(a, (int)grid, c.block, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "axis launch: %s", cudaGetErrorString(err));
+    if (a.splits > 1) {
+        const KernelEntry* f = reg_find(KernelKey{K_AXIS_FINISH, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec,
+                                                  (uint8_t)aux, 0, 0});
+        if (!f) return fail(PR_ERR_UNSUPPORTED, "no axis finishing kernel");
+        const int64_t fgrid = (outer * inner * 32 + 255) / 256;
+        if (fgrid > 0x7fffffff) return fail(PR_ERR_INVALID, "axis reduction too large for one launch");
+        err = reinterpret_cast<AxisLaunch>(f->launch)(a, (int)fgrid, 256, st);
+        if (err != cudaSuccess) return fail(PR_ERR_CUDA, "axis finish launch: %s", cudaGetErrorString(err));
+    }
+    return PR_OK;
+}
+
+static pr_status run_axis_backward(int op, int dtype, const void* x, int64_t outer, int64_t n, int64_t inner,
+                                   const void* g, const int64_t* argidx, const pr_prod_aux* aux, void* gi,
+                                   cudaStream_t st) {
+    DevInfo di;
+    pr_status s = device_info(&di, nullptr);
+    if (s != PR_OK) return s;
+    const int es = elem_size(dtype);
+    int vb = 32;
+    if (inner % (vb / es) != 0 || reinterpret_cast<uintptr_t>(gi) % 32 != 0) vb = 16;
+    if (inner % (vb / es) != 0 || reinterpret_cast<uintptr_t>(gi) % 16 != 0) vb = 0;
+    const KernelEntry* e = reg_find(KernelKey{K_AXIS_BACKWARD, (uint8_t)dtype, 0, 0, 0, 0, (uint8_t)vb});
+    if (!e) return fail(PR_ERR_UNSUPPORTED, "no axis backward kernel for dtype %d", dtype);
+    const int ve = vb ? vb / es : 1;
+    AxisBwdArgs a{x, g, argidx, aux, gi, outer, n, inner, inner / ve, op};
+    const int64_t total = outer * n * a.qv;
+    int64_t grid = (total + 255) / 256;
+    const int64_t cap = (int64_t)di.sms * 64;
+    if (grid > cap) grid = cap;
+    cudaError_t err = reinterpret_cast<AxisBwdLaunch>(e->launch)(a, (int)grid, 256, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "axis backward launch: %s", cudaGetErrorString(err));
+    return PR_OK;
+}
+
 // ------------------------------------------------------------------------
 // Validation shared by the entry points
 // ------------------------------------------------------------------------
@@ -567,6 +698,53 @@ pr_status pr_reduce_backward(pr_op op, pr_dtype dtype, const void* x, int64_t ro
     return run_backward(op, dtype, x, rows, cols, grad_out, argidx, aux, grad_in, (cudaStream_t)stream, c);
 }
 
+pr_status pr_reduce_axis(const void* x, int64_t outer, int64_t n, int64_t inner, pr_dtype dtype, pr_op op,
+                         pr_precision precision, void* out, int64_t* argidx, pr_prod_aux* aux, pr_stream_t stream) {
+    g_msg.clear();
+    if (outer < 0 || n < 0 || inner < 0) return fail(PR_ERR_INVALID, "outer, n and inner must be >= 0");
+    const int64_t lim = (int64_t)1 << 62;
+    if ((outer > 0 && inner > 0 && (outer > lim / inner || (n > 0 && outer * inner > lim / n))))
+        return fail(PR_ERR_INVALID, "outer*n*inner overflows");
+    pr_status s = check_common(dtype, op, precision);
+    if (s != PR_OK) return s;
+    if (argidx && op != PR_MAX && op != PR_MIN) return fail(PR_ERR_UNSUPPORTED, "argidx needs MAX or MIN");
+    if (aux && !(op == PR_PROD && (dtype == PR_F32 || dtype == PR_F64)))
+        return fail(PR_ERR_UNSUPPORTED, "product aux needs PROD on F32 or F64");
+    if (outer == 0 || inner == 0) return PR_OK;
+    if (!out) return fail(PR_ERR_INVALID, "out is NULL");
+    if (n > 0 && !x) return fail(PR_ERR_INVALID, "x is NULL");
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    if (inner == 1) return pr_reduce_rows(x, outer, n, dtype, op, precision, out, argidx, aux, stream);
+    ensure_registered();
+    const int auxk = argidx ? AUX_ARG : (aux ? AUX_PROD : AUX_NONE);
+    const pr_config c = lookup_cfg(PR_KIND_AXIS, dtype, op, precision, outer * n * inner);
+    return run_axis(x, outer, n, inner, dtype, op, precision, auxk, out, argidx, aux, (cudaStream_t)stream, c);
+}
+
+pr_status pr_reduce_axis_backward(pr_op op, pr_dtype dtype, const void* x, int64_t outer, int64_t n, int64_t inner,
+                                  const void* grad_out, const int64_t* argidx, const pr_prod_aux* aux,
+                                  void* grad_in, pr_stream_t stream) {
+    g_msg.clear();
+    if (dtype != PR_F32 && dtype != PR_F64) return fail(PR_ERR_UNSUPPORTED, "backward supports F32 and F64");
+    if (op != PR_SUM && op != PR_MAX && op != PR_MIN && op != PR_PROD)
+        return fail(PR_ERR_UNSUPPORTED, "backward supports SUM, MAX, MIN and PROD");
+    if (outer < 0 || n < 0 || inner < 0) return fail(PR_ERR_INVALID, "outer, n and inner must be >= 0");
+    const int64_t lim = (int64_t)1 << 62;
+    if ((outer > 0 && inner > 0 && (outer > lim / inner || (n > 0 && outer * inner > lim / n))))
+        return fail(PR_ERR_INVALID, "outer*n*inner overflows");
+    if (outer == 0 || n == 0 || inner == 0) return PR_OK;
+    if (inner == 1) return pr_reduce_backward(op, dtype, x, outer, n, grad_out, argidx, aux, grad_in, stream);
+    if (!grad_out || !grad_in) return fail(PR_ERR_INVALID, "grad_out / grad_in is NULL");
+    if ((op == PR_MAX || op == PR_MIN) && !argidx) return fail(PR_ERR_INVALID, "MAX/MIN backward needs argidx");
+    if (op == PR_PROD && (!aux || !x)) return fail(PR_ERR_INVALID, "PROD backward needs x and aux");
+    pr_status s;
+    if ((s = check_aligned(grad_in, dtype, "grad_in")) != PR_OK) return s;
+    if ((s = check_aligned(grad_out, dtype, "grad_out")) != PR_OK) return s;
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    ensure_registered();
+    return run_axis_backward(op, dtype, x, outer, n, inner, grad_out, argidx, aux, grad_in, (cudaStream_t)stream);
+}
+
 pr_status pr_prepare(pr_stream_t stream) {
     g_msg.clear();
     ensure_registered();
@@ -685,7 +863,7 @@ pr_status pr_reduce_host(const void* host_x, int64_t n, pr_dtype dtype, pr_op op
 pr_status pr_get_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision precision, int64_t n, pr_config* cfg) {
     g_msg.clear();
     if (!cfg) return fail(PR_ERR_INVALID, "cfg is NULL");
-    if (kind < PR_KIND_REDUCE || kind > PR_KIND_ROWS) return fail(PR_ERR_INVALID, "unknown kind");
+    if (kind < PR_KIND_REDUCE || kind > PR_KIND_AXIS) return fail(PR_ERR_INVALID, "unknown kind");
     *cfg = lookup_cfg(kind, dtype, op, precision, n);
     return PR_OK;
 }
@@ -693,7 +871,7 @@ pr_status pr_get_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision pre
 pr_status pr_set_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision precision, int64_t n,
                         const pr_config* cfg) {
     g_msg.clear();
-    if (kind < PR_KIND_REDUCE || kind > PR_KIND_ROWS) return fail(PR_ERR_INVALID, "unknown kind");
+    if (kind < PR_KIND_REDUCE || kind > PR_KIND_AXIS) return fail(PR_ERR_INVALID, "unknown kind");
     if (!cfg || !cfg_valid(*cfg, kind)) return fail(PR_ERR_INVALID, "invalid configuration for kind %d", kind);
     std::lock_guard<std::mutex> lk(g_mu);
     g_tuned[CfgKey{kind, dtype, op, precision, bucket_of(n)}] = *cfg;

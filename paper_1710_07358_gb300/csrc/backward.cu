@@ -14,6 +14,7 @@
 // are re-read only when a block's row changes.
 #include "registry.h"
 #include "kernels.cuh"
+#include "axis.cuh"
 
 namespace pr {
 
@@ -142,7 +143,26 @@ static void reg_bwd(uint8_t dtype) {
                         reinterpret_cast<void*>(&launch_backward<F, U, VB>)});
 }
 
+template <class F, int VB>
+cudaError_t launch_axis_backward(const AxisBwdArgs& a, int grid, int block, cudaStream_t st) {
+    k_axis_backward<F, VB><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class F, int VB>
+static void reg_axis_bwd(uint8_t dtype) {
+    reg_add(KernelKey{K_AXIS_BACKWARD, dtype, 0, 0, 0, 0, (uint8_t)VB},
+            KernelEntry{reinterpret_cast<const void*>(&k_axis_backward<F, VB>),
+                        reinterpret_cast<void*>(&launch_axis_backward<F, VB>)});
+}
+
 void register_backward() {
+    reg_axis_bwd<float, 0>(PR_F32);
+    reg_axis_bwd<float, 16>(PR_F32);
+    reg_axis_bwd<float, 32>(PR_F32);
+    reg_axis_bwd<double, 0>(PR_F64);
+    reg_axis_bwd<double, 16>(PR_F64);
+    reg_axis_bwd<double, 32>(PR_F64);
     reg_bwd<float, 2, 16>(PR_F32);
     reg_bwd<float, 2, 32>(PR_F32);
     reg_bwd<float, 4, 16>(PR_F32);

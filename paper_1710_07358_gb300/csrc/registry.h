@@ -11,9 +11,14 @@ namespace pr {
 struct ReduceArgs;
 struct SegArgs;
 struct RowArgs;
+struct AxisArgs;
+struct AxisBwdArgs;
 struct BwdArgs;
 
-enum Kind : uint8_t { K_REDUCE = 0, K_SEGMENTED = 1, K_BACKWARD = 2, K_COMBINE = 3, K_ROWS = 4 };
+enum Kind : uint8_t {
+    K_REDUCE = 0, K_SEGMENTED = 1, K_BACKWARD = 2, K_COMBINE = 3, K_ROWS = 4,
+    K_AXIS = 5, K_AXIS_FINISH = 6, K_AXIS_EMPTY = 7, K_AXIS_BACKWARD = 8
+};
 enum Aux : uint8_t { AUX_NONE = 0, AUX_ARG = 1, AUX_PROD = 2 };
 
 struct KernelKey {
@@ -24,12 +29,15 @@ struct KernelKey {
 using ReduceLaunch = cudaError_t (*)(const ReduceArgs&, int grid, int block, cudaStream_t);
 using SegLaunch = cudaError_t (*)(const SegArgs&, int grid, int block, cudaStream_t);
 using RowLaunch = cudaError_t (*)(const RowArgs&, int grid, int block, cudaStream_t);
+using AxisLaunch = cudaError_t (*)(const AxisArgs&, int grid, int block, cudaStream_t);
+using AxisBwdLaunch = cudaError_t (*)(const AxisBwdArgs&, int grid, int block, cudaStream_t);
 using BwdLaunch = cudaError_t (*)(const BwdArgs&, int grid, int block, cudaStream_t);
 using CombineLaunch = cudaError_t (*)(const char* parts, int count, void* out, int out_f64, cudaStream_t);
 
 struct KernelEntry {
     const void* fn;      // the __global__ function (occupancy queries)
     void* launch;        // one of the *Launch types above, by kind
+    int part_bytes = 0;  // K_AXIS: bytes of one cross-warp partial
 };
 
 void reg_add(const KernelKey& k, const KernelEntry& e);

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libpr.so")
 DTYPES = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3, "i32": 4, "u32": 5, "i64": 6}
 OPS = {"sum": 0, "prod": 1, "max": 2, "min": 3, "and": 4, "or": 5, "xor": 6}
 PRECISIONS = {"plain": 0, "compensated": 1, "fp64_combine": 2}
-KINDS = {"reduce": 0, "segmented": 1, "backward": 2, "rows": 3}
+KINDS = {"reduce": 0, "segmented": 1, "backward": 2, "rows": 3, "axis": 4}
 STATUS = {0: "PR_OK", 1: "PR_ERR_INVALID", 2: "PR_ERR_UNSUPPORTED", 3: "PR_ERR_CUDA",
           4: "PR_ERR_TIMEOUT", 5: "PR_ERR_NOMEM"}
 ELEM_SIZE = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "i32": 4, "u32": 4, "i64": 8}
@@ -55,6 +55,8 @@ _SIGS = {
     "pr_segmented_reduce_aux": [_P, _P, _I64, _I, _I, _I, _P, _P, _P, _P],
     "pr_reduce_rows": [_P, _I64, _I64, _I, _I, _I, _P, _P, _P, _P],
     "pr_reduce_backward": [_I, _I, _P, _I64, _I64, _P, _P, _P, _P, _P],
+    "pr_reduce_axis": [_P, _I64, _I64, _I64, _I, _I, _I, _P, _P, _P, _P],
+    "pr_reduce_axis_backward": [_I, _I, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P],
     "pr_reduce_host": [_P, _I64, _I, _I, _P, _P],
     "pr_reduce_noalloc": [_P, _I64, _I, _I, _P, _P],
     "pr_prepare": [_P],
@@ -135,6 +137,14 @@ def pr_reduce_rows(x, rows, cols, dtype, op, precision, out, argidx, aux, stream
 
 def pr_reduce_backward(op, dtype, x, rows, cols, grad_out, argidx, aux, grad_in, stream):
     return lib().pr_reduce_backward(op, dtype, x, rows, cols, grad_out, argidx, aux, grad_in, stream)
+
+
+def pr_reduce_axis(x, outer, n, inner, dtype, op, precision, out, argidx, aux, stream):
+    return lib().pr_reduce_axis(x, outer, n, inner, dtype, op, precision, out, argidx, aux, stream)
+
+
+def pr_reduce_axis_backward(op, dtype, x, outer, n, inner, grad_out, argidx, aux, grad_in, stream):
+    return lib().pr_reduce_axis_backward(op, dtype, x, outer, n, inner, grad_out, argidx, aux, grad_in, stream)
 
 
 def pr_reduce_host(host_x, n, dtype, op, host_out, stream):
@@ -308,6 +318,56 @@ def reduce_rows(x, op: str, precision: str = "plain", argidx: bool = False, aux:
     if aux:
         return out, ax
     return out
+
+
+def axis_shape(shape, dim):
+    """(outer, n, inner) of a reduction of `dim` over a contiguous tensor of `shape`."""
+    dim = dim % len(shape)
+    outer = 1
+    for v in shape[:dim]:
+        outer *= v
+    inner = 1
+    for v in shape[dim + 1:]:
+        inner *= v
+    return outer, shape[dim], inner
+
+
+def reduce_axis(x, op: str, dim: int, precision: str = "plain", argidx: bool = False, aux: bool = False,
+                stream=None):
+    """Reduce a contiguous CUDA tensor along `dim` (the other dimensions kept).
+
+    Returns out, or (out, argidx) / (out, aux) when requested, shaped like x
+    without `dim`; aux is an int8 tensor of 24-byte pr_prod_aux records."""
+    torch = _torch()
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("reduce_axis needs a contiguous CUDA tensor")
+    d = dtype_name(x)
+    outer, n, inner = axis_shape(tuple(x.shape), dim)
+    oshape = tuple(v for i, v in enumerate(x.shape) if i != dim % x.dim())
+    out = torch.empty(oshape, dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
+    ai = torch.empty(oshape, dtype=torch.int64, device=x.device) if argidx else None
+    ax = torch.empty(outer * inner * 24, dtype=torch.int8, device=x.device) if aux else None
+    check(pr_reduce_axis(_ptr(x), outer, n, inner, DTYPES[d], OPS[op], PRECISIONS[precision], _ptr(out), _ptr(ai),
+                         _ptr(ax), _stream(x, stream)))
+    if argidx:
+        return out, ai
+    if aux:
+        return out, ax
+    return out
+
+
+def reduce_axis_backward(op: str, x, dim: int, grad_out, argidx=None, aux=None, out=None, stream=None):
+    """grad_in (x's shape) for reduce_axis(x, op, dim); x is read only for prod
+    (anything with .shape and .data_ptr() serves otherwise)."""
+    torch = _torch()
+    d = dtype_name(grad_out)
+    shape = tuple(x.shape)
+    outer, n, inner = axis_shape(shape, dim)
+    gi = out if out is not None else torch.empty(shape, dtype=grad_out.dtype, device=grad_out.device)
+    xp = _ptr(x) if op == "prod" else None
+    check(pr_reduce_axis_backward(OPS[op], DTYPES[d], xp, outer, n, inner, _ptr(grad_out.contiguous()),
+                                  _ptr(argidx), _ptr(aux), _ptr(gi), _stream(grad_out, stream)))
+    return gi
 
 
 def prod_aux_fields(aux):

@@ -109,6 +109,26 @@ def test_rows_and_backward_reject(L):
     assert pr.pr_reduce_backward(SUM, F32, None, 0, 4, None, None, None, None, None) == OK
 
 
+def test_axis_rejects(L):
+    assert pr.pr_reduce_axis(FAKE, -1, 4, 4, F32, SUM, PLAIN, FAKE, None, None, None) == INVALID
+    assert pr.pr_reduce_axis(FAKE, 2, 4, -4, F32, SUM, PLAIN, FAKE, None, None, None) == INVALID
+    assert pr.pr_reduce_axis(FAKE, 2 ** 40, 2 ** 20, 2 ** 10, F32, SUM, PLAIN, FAKE, None, None, None) == INVALID
+    assert pr.pr_reduce_axis(None, 2, 4, 4, F32, SUM, PLAIN, FAKE, None, None, None) == INVALID
+    assert pr.pr_reduce_axis(FAKE, 2, 4, 4, F32, SUM, PLAIN, None, None, None, None) == INVALID
+    assert pr.pr_reduce_axis(FAKE, 2, 4, 4, F32, XOR, PLAIN, FAKE, None, None, None) == UNSUPPORTED
+    assert pr.pr_reduce_axis(FAKE, 2, 4, 4, F32, SUM, PLAIN, FAKE, FAKE, None, None) == UNSUPPORTED
+    assert pr.pr_reduce_axis(FAKE, 2, 4, 4, I32, PROD, PLAIN, FAKE, None, FAKE, None) == UNSUPPORTED
+    assert pr.pr_reduce_axis(FAKE + 2, 2, 4, 4, F32, SUM, PLAIN, FAKE, None, None, None) == INVALID
+    # nothing to compute: no outputs
+    assert pr.pr_reduce_axis(None, 0, 4, 4, F32, SUM, PLAIN, None, None, None, None) == OK
+    assert pr.pr_reduce_axis(None, 3, 4, 0, F32, SUM, PLAIN, None, None, None, None) == OK
+    assert pr.pr_reduce_axis_backward(SUM, I32, FAKE, 2, 4, 4, FAKE, None, None, FAKE, None) == UNSUPPORTED
+    assert pr.pr_reduce_axis_backward(MAX, F32, None, 2, 4, 4, FAKE, None, None, FAKE, None) == INVALID
+    assert pr.pr_reduce_axis_backward(PROD, F32, None, 2, 4, 4, FAKE, None, FAKE, FAKE, None) == INVALID
+    assert pr.pr_reduce_axis_backward(SUM, F32, None, 2, 4, -1, FAKE, None, None, FAKE, None) == INVALID
+    assert pr.pr_reduce_axis_backward(SUM, F32, None, 2, 0, 4, None, None, None, None, None) == OK
+
+
 def test_host_path_rejects(L):
     assert pr.pr_reduce_host(None, 5, F32, SUM, FAKE, None) == INVALID
     assert pr.pr_reduce_host(FAKE, 5, F32, SUM, None, None) == INVALID

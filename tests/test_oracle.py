@@ -371,6 +371,38 @@ def test_segmented_identities_and_totals():
 # Workload generators that the tolerances depend on
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("outer,n,inner", [(3, 17, 5), (1, 40, 1), (4, 1, 9), (2, 6, 13)])
+def test_axis_oracle_matches_library_reductions(outer, n, inner):
+    """Reductions along the middle axis, pinned to numpy's axis reductions on
+    exact (integer) data: a transposed or mis-strided slice fails here."""
+    rng = np.random.default_rng(outer * 100 + n * 10 + inner)
+    xi = rng.integers(-1000, 1000, size=outer * n * inner).astype(np.int32)
+    x3 = xi.reshape(outer, n, inner).astype(np.int64)
+    assert oracle.axis(xi, "i32", "sum", outer, n, inner) == list(x3.sum(axis=1).reshape(-1))
+    assert oracle.axis(xi, "i32", "max", outer, n, inner) == list(x3.max(axis=1).reshape(-1))
+    assert oracle.axis(xi, "i32", "min", outer, n, inner) == list(x3.min(axis=1).reshape(-1))
+    xu = rng.integers(0, 2 ** 32, size=outer * n * inner, dtype=np.uint64).astype(np.uint32)
+    want = np.bitwise_xor.reduce(xu.reshape(outer, n, inner), axis=1).reshape(-1)
+    assert oracle.axis(xu, "u32", "xor", outer, n, inner) == [int(v) for v in want]
+    # first index of the extremum along the axis: numpy's argmax / argmin take the first too
+    am = oracle.axis_argext(xi, "i32", "max", outer, n, inner)
+    assert [i for _, i in am] == list(x3.argmax(axis=1).reshape(-1))
+    an = oracle.axis_argext(xi, "i32", "min", outer, n, inner)
+    assert [i for _, i in an] == list(x3.argmin(axis=1).reshape(-1))
+    # float sums: each output is the exact sum of its column
+    xf = rng.standard_normal(outer * n * inner).astype(np.float32)
+    cols = xf.reshape(outer, n, inner).transpose(0, 2, 1).reshape(-1, n)
+    assert oracle.axis(xf, "f32", "sum", outer, n, inner) == [math.fsum(float(v) for v in c) for c in cols]
+
+
+def test_axis_oracle_empty_axis_and_rows():
+    assert oracle.axis(np.zeros(0, np.float32), "f32", "max", 2, 0, 3) == [-math.inf] * 6
+    assert oracle.axis(np.zeros(0, np.int32), "i32", "sum", 2, 0, 3) == [0] * 6
+    # inner == 1 is the row reduction
+    x = synth.normal_f32(5 * 7, 4)
+    assert oracle.axis(x, "f32", "sum", 5, 7, 1) == oracle.segmented(x, np.arange(6) * 7, "f32", "sum")
+
+
 def test_ill_conditioned_set_cancels_exactly():
     # the exact sum is fixed by construction (pairs cancel, m copies of 2^-10)
     x, n_big, exact = synth.ill_conditioned_f32(2 ** 20, 5)
