@@ -12,7 +12,9 @@ Also reported in the same line:
   cpu_baseline the CPU oracle (exact fixed-point sum, one host core) on the same data;
   forms        every op / dtype of the sweep at 2^28, the precision modes, the
                segmented form (4096 log-uniform segments, autotuned, replayed from a
-               CUDA graph) and forward+backward of [64, 2^20] row reductions.
+               CUDA graph), forward+backward of [64, 2^20] row reductions, and
+               reductions of a non-last axis (1 GiB: middle axis of [16, 4096,
+               4096] with its gradient, first axis of [16384, 16384]).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms]
 
@@ -165,7 +167,7 @@ def cpu_oracle_sum(x):
 # Secondary forms (all on the same GPU, same run)
 # --------------------------------------------------------------------------
 
-FORM_GROUPS = ("plain", "precision", "illcond", "segmented", "fwdbwd")
+FORM_GROUPS = ("plain", "precision", "illcond", "segmented", "fwdbwd", "axis")
 
 
 def forms(steps, warmup, peak, only=None, tune=True):
@@ -225,7 +227,39 @@ def forms(steps, warmup, peak, only=None, tune=True):
         segmented(res, k, warmup, peak, tune)
     if "fwdbwd" in want:
         fwdbwd(res, k, warmup, peak, st, g)
+    if "axis" in want:
+        axis(res, k, warmup, peak, st, g)
     return res
+
+
+def axis(res, k, warmup, peak, st, g):
+    """Reductions of a non-last axis, 1 GiB each: the middle axis of
+    [16, 4096, 4096] fp32 (sum; max with its first index) and its gradient,
+    and the first axis of [16384, 16384] (a column reduction)."""
+    import torch
+    from paper_1710_07358_gb300 import pr
+    dev = torch.device("cuda")
+    g.manual_seed(7)
+    x = torch.randn(16, 4096, 4096, generator=g, device=dev)
+    nb = x.numel() * 4
+
+    def put(name, per, nbytes):
+        res[name] = {"GB/s": round(gbs(nbytes, per), 1), "frac": round(gbs(nbytes, per) / peak, 4),
+                     "us": round(per * 1e3, 2)}
+
+    _, per = time_launches(lambda: pr.reduce_axis(x, "sum", 1), k, warmup, st)
+    put("axis_mid_sum", per, nb)
+    _, per = time_launches(lambda: pr.reduce_axis(x, "max", 1, argidx=True), k, warmup, st)
+    put("axis_mid_max_arg", per, nb)
+    gout = torch.randn(16, 4096, generator=g, device=dev)
+    gi = torch.empty_like(x)
+    _, per = time_launches(lambda: pr.reduce_axis_backward("sum", x, 1, gout, out=gi), k, warmup, st)
+    put("axis_mid_sum_bwd", per, nb)
+    del x, gi
+    c = torch.randn(16384, 16384, generator=g, device=dev)
+    _, per = time_launches(lambda: pr.reduce_axis(c, "sum", 0), k, warmup, st)
+    put("axis_col_sum", per, c.numel() * 4)
+    del c
 
 
 def ill(res, k, warmup, peak, st):

@@ -294,6 +294,13 @@ pr_status pr_set_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision pre
 pr_status pr_autotune(pr_kind kind, const void* x, int64_t n, const int64_t* offsets,
                       int64_t nseg, pr_dtype dtype, pr_op op, pr_precision precision,
                       pr_stream_t stream, pr_config* best);
+
+/* pr_autotune for PR_KIND_AXIS: x of shape [outer, n, inner] (inner > 1),
+ * timed with the outputs the differentiation forward uses (argidx for
+ * MAX/MIN, aux for PROD on F32/F64); keeps the winner for outer*n*inner's
+ * bucket.  Same blocking and capture rules as pr_autotune. */
+pr_status pr_autotune_axis(const void* x, int64_t outer, int64_t n, int64_t inner, pr_dtype dtype,
+                           pr_op op, pr_precision precision, pr_stream_t stream, pr_config* best);
 /* Persist / restore the tuned table (a small JSON file, keyed by GPU name). */
 pr_status pr_tune_save(const char* path);
 pr_status pr_tune_load(const char* path);

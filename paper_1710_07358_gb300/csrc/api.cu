@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -513,9 +514,15 @@ static pr_status run_axis_backward(int op, int dtype, const void* x, int64_t out
     if (s != PR_OK) return s;
     const int es = elem_size(dtype);
     int vb = 32;
-    if (inner % (vb / es) != 0 || reinterpret_cast<uintptr_t>(gi) % 32 != 0) vb = 16;
-    if (inner % (vb / es) != 0 || reinterpret_cast<uintptr_t>(gi) % 16 != 0) vb = 0;
-    const KernelEntry* e = reg_find(KernelKey{K_AXIS_BACKWARD, (uint8_t)dtype, 0, 0, 0, 0, (uint8_t)vb});
+    // vectors need grad_in and grad_out aligned to them and whole vectors per row
+    auto fits = [&](int w) {
+        return inner % (w / es) == 0 && reinterpret_cast<uintptr_t>(gi) % (uintptr_t)w == 0 &&
+               reinterpret_cast<uintptr_t>(g) % (uintptr_t)w == 0;
+    };
+    if (!fits(vb)) vb = 16;
+    if (!fits(vb)) vb = 0;
+    const int opk = op == PR_SUM ? 0 : (op == PR_PROD ? 2 : 1);
+    const KernelEntry* e = reg_find(KernelKey{K_AXIS_BACKWARD, (uint8_t)dtype, (uint8_t)opk, 0, 0, 0, (uint8_t)vb});
     if (!e) return fail(PR_ERR_UNSUPPORTED, "no axis backward kernel for dtype %d", dtype);
     const int ve = vb ? vb / es : 1;
     AxisBwdArgs a{x, g, argidx, aux, gi, outer, n, inner, inner / ve, op};
@@ -878,13 +885,64 @@ pr_status pr_set_config(pr_kind kind, pr_dtype dtype, pr_op op, pr_precision pre
     return PR_OK;
 }
 
+// Time every candidate configuration of `kind` with CUDA events on st (two
+// warm-up runs, best of five) and return the fastest; *best_ms stays 1e30
+// when no candidate could run.
+static pr_status tune_candidates(int kind, cudaStream_t st, const std::function<pr_status(const pr_config&)>& run,
+                                 pr_config* best_c, float* best_ms) {
+    cudaEvent_t e0, e1;
+    PR_CUDA(cudaEventCreate(&e0));
+    PR_CUDA(cudaEventCreate(&e1));
+    *best_ms = 1e30f;
+    const int blocks[] = {64, 128, 256, 512, 1024};
+    const int bpss[] = {1, 2, 4, 8};
+    pr_status s = PR_OK;
+    for (int blk : blocks)
+        for (int bps : bpss) {
+            if (blk * bps > 2048 || !cfg_valid(pr_config{blk, bps, 2, 16}, kind)) continue;
+            if (blk == 64 && kind != PR_KIND_AXIS) continue;
+            for (int u : kUnrolls)
+                for (int vb : kVecBytes) {
+                    const pr_config c{blk, bps, u, vb};
+                    bool ok = true;
+                    for (int w = 0; w < 2 && ok; w++) ok = run(c) == PR_OK;
+                    if (!ok) continue;
+                    float t_min = 1e30f;
+                    for (int r = 0; r < 5 && ok; r++) {
+                        if (cudaEventRecord(e0, st) != cudaSuccess) { s = PR_ERR_CUDA; break; }
+                        ok = run(c) == PR_OK;
+                        cudaEventRecord(e1, st);
+                        cudaEventSynchronize(e1);
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        t_min = ms < t_min ? ms : t_min;
+                    }
+                    if (ok && t_min < *best_ms) {
+                        *best_ms = t_min;
+                        *best_c = c;
+                    }
+                }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s == PR_OK ? PR_OK : fail(s, "autotune: a CUDA event call failed");
+}
+
+static void keep_tuned(int kind, int dtype, int op, int prec, int64_t bucket_n, const pr_config& c, float best_ms) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const CfgKey key{kind, dtype, op, prec, bucket_of(bucket_n)};
+    if (best_ms >= 1e30f) g_tuned.erase(key);   // no candidate ran: keep the default
+    else g_tuned[key] = c;
+}
+
 pr_status pr_autotune(pr_kind kind, const void* x, int64_t n, const int64_t* offsets, int64_t nseg, pr_dtype dtype,
                       pr_op op, pr_precision precision, pr_stream_t stream, pr_config* best) {
     g_msg.clear();
     pr_status s = check_common(dtype, op, precision);
     if (s != PR_OK) return s;
     if (kind != PR_KIND_REDUCE && kind != PR_KIND_SEGMENTED && kind != PR_KIND_ROWS)
-        return fail(PR_ERR_UNSUPPORTED, "autotune covers PR_KIND_REDUCE, PR_KIND_SEGMENTED and PR_KIND_ROWS");
+        return fail(PR_ERR_UNSUPPORTED, "autotune covers PR_KIND_REDUCE, PR_KIND_SEGMENTED and PR_KIND_ROWS "
+                                        "(pr_autotune_axis for PR_KIND_AXIS)");
     if (kind == PR_KIND_REDUCE && (n <= 0 || !x)) return fail(PR_ERR_INVALID, "autotune needs data (x, n > 0)");
     if (kind == PR_KIND_SEGMENTED && (nseg <= 0 || !offsets || !x))
         return fail(PR_ERR_INVALID, "autotune needs x, offsets and nseg > 0");
@@ -904,61 +962,55 @@ pr_status pr_autotune(pr_kind kind, const void* x, int64_t n, const int64_t* off
     PR_CUDA(cudaMalloc(&dout, (size_t)nout * (8 + sizeof(pr_prod_aux))));
     int64_t* dargs = reinterpret_cast<int64_t*>(static_cast<char*>(dout) + nout * 8);
     pr_prod_aux* daux = reinterpret_cast<pr_prod_aux*>(static_cast<char*>(dout) + nout * 8);
-    cudaEvent_t e0, e1;
-    PR_CUDA(cudaEventCreate(&e0));
-    PR_CUDA(cudaEventCreate(&e1));
-    const bool f64 = false;
-    float best_ms = 1e30f;
     pr_config best_c = default_cfg(kind, dtype, op, precision);
-    const int blocks[] = {128, 256, 512, 1024};
-    const int bpss[] = {1, 2, 4, 8};
-    for (int blk : blocks)
-        for (int bps : bpss) {
-            if (blk * bps > 2048 || !cfg_valid(pr_config{blk, bps, 2, 16}, kind)) continue;
-            for (int u : kUnrolls)
-                for (int vb : kVecBytes) {
-                    const pr_config c{blk, bps, u, vb};
-                    auto run = [&]() -> pr_status {
-                        if (kind == PR_KIND_REDUCE)
-                            return run_reduce(x, n, dtype, op, precision, f64, dout, nullptr, st, c);
-                        if (kind == PR_KIND_ROWS)
-                            return run_rows(x, nseg, n / nseg, dtype, op, precision, row_aux, dout,
-                                            row_aux == AUX_ARG ? dargs : nullptr,
-                                            row_aux == AUX_PROD ? daux : nullptr, st, c);
-                        return run_segmented(x, offsets, 0, nseg, dtype, op, precision, AUX_NONE, dout, nullptr,
-                                             nullptr, st, c);
-                    };
-                    bool ok = true;
-                    for (int w = 0; w < 2 && ok; w++) ok = run() == PR_OK;
-                    if (!ok) continue;
-                    float t_min = 1e30f;
-                    for (int r = 0; r < 5 && ok; r++) {
-                        PR_CUDA(cudaEventRecord(e0, st));
-                        ok = run() == PR_OK;
-                        PR_CUDA(cudaEventRecord(e1, st));
-                        PR_CUDA(cudaEventSynchronize(e1));
-                        float ms = 0;
-                        PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                        t_min = ms < t_min ? ms : t_min;
-                    }
-                    if (ok && t_min < best_ms) {
-                        best_ms = t_min;
-                        best_c = c;
-                    }
-                }
-        }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    float best_ms = 1e30f;
+    s = tune_candidates(kind, st, [&](const pr_config& c) -> pr_status {
+        if (kind == PR_KIND_REDUCE) return run_reduce(x, n, dtype, op, precision, false, dout, nullptr, st, c);
+        if (kind == PR_KIND_ROWS)
+            return run_rows(x, nseg, n / nseg, dtype, op, precision, row_aux, dout, row_aux == AUX_ARG ? dargs : nullptr,
+                            row_aux == AUX_PROD ? daux : nullptr, st, c);
+        return run_segmented(x, offsets, 0, nseg, dtype, op, precision, AUX_NONE, dout, nullptr, nullptr, st, c);
+    }, &best_c, &best_ms);
     cudaFree(dout);
+    if (s != PR_OK) return s;
     g_msg.clear();
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        g_tuned[CfgKey{kind, dtype, op, precision, bucket_of(kind == PR_KIND_SEGMENTED ? nseg : n)}] = best_c;
-        if (best_ms >= 1e30f) {
-            // no candidate ran (rows that need the segmented kernel): keep the default
-            g_tuned.erase(CfgKey{kind, dtype, op, precision, bucket_of(kind == PR_KIND_SEGMENTED ? nseg : n)});
-        }
-    }
+    keep_tuned(kind, dtype, op, precision, kind == PR_KIND_SEGMENTED ? nseg : n, best_c, best_ms);
+    if (best) *best = best_c;
+    return PR_OK;
+}
+
+pr_status pr_autotune_axis(const void* x, int64_t outer, int64_t n, int64_t inner, pr_dtype dtype, pr_op op,
+                           pr_precision precision, pr_stream_t stream, pr_config* best) {
+    g_msg.clear();
+    pr_status s = check_common(dtype, op, precision);
+    if (s != PR_OK) return s;
+    if (outer <= 0 || n <= 0 || inner <= 1 || !x)
+        return fail(PR_ERR_INVALID, "axis autotune needs x, outer > 0, n > 0 and inner > 1");
+    const int64_t lim = (int64_t)1 << 62;
+    if (outer > lim / inner || outer * inner > lim / n) return fail(PR_ERR_INVALID, "outer*n*inner overflows");
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    ensure_registered();
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    PR_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return fail(PR_ERR_INVALID, "autotune cannot run during capture");
+    const int aux = (op == PR_MAX || op == PR_MIN) ? AUX_ARG
+                    : (op == PR_PROD && (dtype == PR_F32 || dtype == PR_F64)) ? AUX_PROD : AUX_NONE;
+    const int64_t nout = outer * inner;
+    void* dout = nullptr;
+    PR_CUDA(cudaMalloc(&dout, (size_t)nout * (8 + sizeof(pr_prod_aux))));
+    int64_t* dargs = reinterpret_cast<int64_t*>(static_cast<char*>(dout) + nout * 8);
+    pr_prod_aux* daux = reinterpret_cast<pr_prod_aux*>(static_cast<char*>(dout) + nout * 8);
+    pr_config best_c = default_cfg(PR_KIND_AXIS, dtype, op, precision);
+    float best_ms = 1e30f;
+    s = tune_candidates(PR_KIND_AXIS, st, [&](const pr_config& c) -> pr_status {
+        return run_axis(x, outer, n, inner, dtype, op, precision, aux, dout, aux == AUX_ARG ? dargs : nullptr,
+                        aux == AUX_PROD ? daux : nullptr, st, c);
+    }, &best_c, &best_ms);
+    cudaFree(dout);
+    if (s != PR_OK) return s;
+    g_msg.clear();
+    keep_tuned(PR_KIND_AXIS, dtype, op, precision, outer * n * inner, best_c, best_ms);
     if (best) *best = best_c;
     return PR_OK;
 }

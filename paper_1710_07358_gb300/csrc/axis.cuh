@@ -37,6 +37,19 @@ struct AxisArgs {
     char* scratch;            // splits > 1: partials [p][q][split] of GridR<T>::Part
 };
 
+// A column's elements reach its accumulator in increasing index order, so a
+// trait may take them with a cheaper in-order step (add_ordered).
+template <class T, class = void>
+struct HasOrdered : std::false_type {};
+template <class T>
+struct HasOrdered<T, std::void_t<decltype(&T::add_ordered)>> : std::true_type {};
+
+template <class T>
+__device__ __forceinline__ void add_in_order(typename T::Acc& a, typename T::Ld::E v, int64_t i) {
+    if constexpr (HasOrdered<T>::value) T::add_ordered(a, v, i);
+    else T::add(a, v, i);
+}
+
 template <int VB, class Ld>
 __device__ __forceinline__ void axis_load(const typename Ld::In* x, int64_t e0, typename Ld::E (&e)[VB ? VB / Ld::ES : 1]) {
     if constexpr (VB == 0) {
@@ -84,13 +97,13 @@ __global__ void __launch_bounds__(MaxBlock<T>::value) k_axis(AxisArgs a) {
 #pragma unroll
             for (int u = 0; u < U; u++)
 #pragma unroll
-                for (int k = 0; k < VE; k++) T::add(acc[k], e[u][k], r + (int64_t)u * ry);
+                for (int k = 0; k < VE; k++) add_in_order<T>(acc[k], e[u][k], r + (int64_t)u * ry);
         }
         for (; r < r1; r += ry) {
             E e[VE];
             axis_load<VB, Ld>(x, slab + r * a.inner, e);
 #pragma unroll
-            for (int k = 0; k < VE; k++) T::add(acc[k], e[k], r);
+            for (int k = 0; k < VE; k++) add_in_order<T>(acc[k], e[k], r);
         }
     }
     const bool f64 = a.out_f64 != 0;
@@ -151,8 +164,10 @@ struct AxisBwdArgs {
 
 // grad_in viewed as rows (p, i) of qv vectors; a thread walks the flattened
 // vectors with a grid stride, advancing (p, i, column) by carries instead of
-// dividing per vector.
-template <class F, int VB>
+// dividing per vector.  OPK: 0 sum (broadcast), 1 max/min (one-hot at argidx),
+// 2 prod (zero-count aware).  With VB > 0, grad_out (and argidx) are read as
+// vectors of the same columns.
+template <class F, int VB, int OPK>
 __global__ void __launch_bounds__(256) k_axis_backward(AxisBwdArgs a) {
     constexpr int VE = VB ? VB / (int)sizeof(F) : 1;
     const F* g = static_cast<const F*>(a.g);
@@ -162,7 +177,6 @@ __global__ void __launch_bounds__(256) k_axis_backward(AxisBwdArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= total) return;
-    // position of v, and the stride split the same way
     int64_t R = v / a.qv, cq = v - R * a.qv;
     int64_t p = R / a.n, i = R - p * a.n;
     const int64_t dR = stride / a.qv, dq = stride - dR * a.qv;
@@ -170,23 +184,28 @@ __global__ void __launch_bounds__(256) k_axis_backward(AxisBwdArgs a) {
     for (; v < total; v += stride) {
         const int64_t o0 = p * a.inner + cq * VE;        // first output of this vector's columns
         const int64_t e0 = (p * a.n + i) * a.inner + cq * VE;
+        F gv[VE];
+        if constexpr (VB == 0) {
+            gv[0] = g[o0];
+        } else {
+            const Words<VB> w = ldv<VB>(g + o0);
+            memcpy(gv, w.w, VB);
+        }
         F vals[VE];
+        if constexpr (OPK == 0) {
 #pragma unroll
-        for (int k = 0; k < VE; k++) {
-            const F gv = g[o0 + k];
-            F r;
-            if (a.op == PR_SUM) {
-                r = gv;
-            } else if (a.op == PR_MAX || a.op == PR_MIN) {
-                r = a.argidx[o0 + k] == i ? gv : (F)0;
-            } else {
+            for (int k = 0; k < VE; k++) vals[k] = gv[k];
+        } else if constexpr (OPK == 1) {
+#pragma unroll
+            for (int k = 0; k < VE; k++) vals[k] = __ldg(a.argidx + o0 + k) == i ? gv[k] : (F)0;
+        } else {
+#pragma unroll
+            for (int k = 0; k < VE; k++) {
                 const pr_prod_aux ax = a.aux[o0 + k];
-                const F gp = (F)((double)gv * ax.p_nz);
-                if (ax.zero_count == 0) r = gp / x[e0 + k];
-                else if (ax.zero_count == 1) r = ax.first_zero == i ? gp : (F)0;
-                else r = (F)0;
+                const F gp = (F)((double)gv[k] * ax.p_nz);
+                vals[k] = ax.zero_count == 0 ? gp / x[e0 + k]
+                          : (ax.zero_count == 1 && ax.first_zero == i ? gp : (F)0);
             }
-            vals[k] = r;
         }
         if constexpr (VB == 0) {
             gi[e0] = vals[0];
@@ -207,7 +226,7 @@ __global__ void __launch_bounds__(256) k_axis_backward(AxisBwdArgs a) {
         }
         // advance by the stride: columns, then rows, then slabs
         cq += dq;
-        int64_t c1 = cq >= a.qv ? 1 : 0;
+        const int64_t c1 = cq >= a.qv ? 1 : 0;
         cq -= c1 * a.qv;
         i += di + c1;
         const int64_t c2 = i >= a.n ? 1 : 0;

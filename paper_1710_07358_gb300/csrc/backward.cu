@@ -143,17 +143,24 @@ static void reg_bwd(uint8_t dtype) {
                         reinterpret_cast<void*>(&launch_backward<F, U, VB>)});
 }
 
-template <class F, int VB>
+template <class F, int VB, int OPK>
 cudaError_t launch_axis_backward(const AxisBwdArgs& a, int grid, int block, cudaStream_t st) {
-    k_axis_backward<F, VB><<<grid, block, 0, st>>>(a);
+    k_axis_backward<F, VB, OPK><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
+// Keyed by (dtype, op kind in the op field: 0 sum, 1 max/min, 2 prod, vector width).
 template <class F, int VB>
 static void reg_axis_bwd(uint8_t dtype) {
     reg_add(KernelKey{K_AXIS_BACKWARD, dtype, 0, 0, 0, 0, (uint8_t)VB},
-            KernelEntry{reinterpret_cast<const void*>(&k_axis_backward<F, VB>),
-                        reinterpret_cast<void*>(&launch_axis_backward<F, VB>)});
+            KernelEntry{reinterpret_cast<const void*>(&k_axis_backward<F, VB, 0>),
+                        reinterpret_cast<void*>(&launch_axis_backward<F, VB, 0>)});
+    reg_add(KernelKey{K_AXIS_BACKWARD, dtype, 1, 0, 0, 0, (uint8_t)VB},
+            KernelEntry{reinterpret_cast<const void*>(&k_axis_backward<F, VB, 1>),
+                        reinterpret_cast<void*>(&launch_axis_backward<F, VB, 1>)});
+    reg_add(KernelKey{K_AXIS_BACKWARD, dtype, 2, 0, 0, 0, (uint8_t)VB},
+            KernelEntry{reinterpret_cast<const void*>(&k_axis_backward<F, VB, 2>),
+                        reinterpret_cast<void*>(&launch_axis_backward<F, VB, 2>)});
 }
 
 void register_backward() {

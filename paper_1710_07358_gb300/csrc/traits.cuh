@@ -566,7 +566,11 @@ struct ArgExt {
 // to 0).  Vectors reach add_vec in increasing index order per accumulator, so
 // only a strictly better key replaces the best vector.  Scalars (head, tail and
 // masked elements), which may arrive out of order, keep their own (key, index)
-// best with the full comparison.  Same result as ArgExt<KeyF32>.
+// best with the full comparison.  Scalars known to arrive in increasing index
+// order per accumulator (add_ordered: the columns of an axis reduction) keep a
+// running max.NaN / min.NaN value and take the index whenever its bits change:
+// max.NaN turns -0 vs +0 and a first NaN into a change of bits, an equal later
+// value into none.  Same result as ArgExt<KeyF32>.
 template <class Ld_, int OutK, bool MX>
 struct ArgExtF {
     using Ld = Ld_;
@@ -584,6 +588,8 @@ struct ArgExtF {
         int64_t iv;       // its first element's index (kNone: none yet)
         uint32_t ks;      // best scalar: key and index
         int64_t is;
+        float sv;         // best in-order scalar: running extremum and its index
+        int64_t so;
     };
     __device__ __forceinline__ static uint32_t raw_key(float v) {
         const uint32_t b = __float_as_uint(v);
@@ -598,11 +604,19 @@ struct ArgExtF {
         a.iv = Base::kNone;
         a.ks = Key::ident(MX);
         a.is = Base::kNone;
+        a.sv = MX ? -INFINITY : INFINITY;
+        a.so = Base::kNone;
         return a;
     }
     __device__ __forceinline__ static void add(Acc& a, E v, int64_t i) {
         const uint32_t k = Key::key(v, MX);
         if (Base::better(k, i, a.ks, a.is)) { a.ks = k; a.is = i; }
+    }
+    __device__ __forceinline__ static void add_ordered(Acc& a, E v, int64_t i) {
+        const float m = MaxMinF<Ld_, OutK, MX>::f(a.sv, v);
+        const bool up = __float_as_uint(m) != __float_as_uint(a.sv) || a.so == Base::kNone;
+        a.so = up ? i : a.so;
+        a.sv = m;
     }
     template <int N>
     __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[N], int64_t i0) {
@@ -624,6 +638,7 @@ struct ArgExtF {
     }
     __device__ __forceinline__ static Part to_part(const Acc& a) {
         Part p{a.ks, a.is};
+        if (a.so != Base::kNone) p = Base::combine(p, Part{Key::key(a.sv, MX), a.so});
         if (a.iv != Base::kNone) {
             const uint32_t kv = MX ? a.kv : (a.kv == 0u ? 0u : a.kv - 1u);   // as Key::key
             int kk = kMaxN - 1;

@@ -64,6 +64,7 @@ _SIGS = {
     "pr_get_config": [_I, _I, _I, _I, _I64, ctypes.POINTER(pr_config)],
     "pr_set_config": [_I, _I, _I, _I, _I64, ctypes.POINTER(pr_config)],
     "pr_autotune": [_I, _P, _I64, _P, _I64, _I, _I, _I, _P, ctypes.POINTER(pr_config)],
+    "pr_autotune_axis": [_P, _I64, _I64, _I64, _I, _I, _I, _P, ctypes.POINTER(pr_config)],
     "pr_tune_save": [ctypes.c_char_p],
     "pr_tune_load": [ctypes.c_char_p],
 }
@@ -189,6 +190,10 @@ def pr_set_config(kind, dtype, op, precision, n, cfg_ref):
 
 def pr_autotune(kind, x, n, offsets, nseg, dtype, op, precision, stream, best_ref):
     return lib().pr_autotune(kind, x, n, offsets, nseg, dtype, op, precision, stream, best_ref)
+
+
+def pr_autotune_axis(x, outer, n, inner, dtype, op, precision, stream, best_ref):
+    return lib().pr_autotune_axis(x, outer, n, inner, dtype, op, precision, stream, best_ref)
 
 
 def pr_tune_save(path):
@@ -433,17 +438,27 @@ def set_config(kind: str, dtype: str, op: str, precision: str, n: int, cfg: dict
     check(pr_set_config(KINDS[kind], DTYPES[dtype], OPS[op], PRECISIONS[precision], n, ctypes.byref(c)))
 
 
-def autotune(kind: str, x, op: str, precision: str = "plain", offsets=None, stream=None) -> dict:
+def autotune(kind: str, x, op: str, precision: str = "plain", offsets=None, stream=None, dim: int = -1) -> dict:
     """Tune (and keep) the configuration for x's size bucket: kind "reduce"
-    (x 1-D), "segmented" (x 1-D plus offsets) or "rows" (x a contiguous
-    [rows, cols] tensor, timed with the differentiation forward's outputs)."""
+    (x 1-D), "segmented" (x 1-D plus offsets), "rows" (x a contiguous
+    [rows, cols] tensor, timed with the differentiation forward's outputs) or
+    "axis" (x contiguous, reduced along `dim`, with the same outputs)."""
     d = dtype_name(x)
     c = pr_config()
     nseg = offsets.numel() - 1 if offsets is not None else 0
+    inner = 0
     if kind == "rows":
         if x.dim() != 2 or not x.is_contiguous():
             raise ValueError("autotune('rows') needs a contiguous 2-D tensor")
         nseg = x.shape[0]
+    if kind == "axis":
+        if not x.is_contiguous():
+            raise ValueError("autotune('axis') needs a contiguous tensor")
+        outer, n, inner = axis_shape(tuple(x.shape), dim)
+        nseg = outer
+        check(pr_autotune_axis(_ptr(x), outer, n, inner, DTYPES[d], OPS[op], PRECISIONS[precision],
+                               _stream(x, stream), ctypes.byref(c)))
+        return c.as_dict()
     check(pr_autotune(KINDS[kind], _ptr(x), x.numel(), _ptr(offsets), nseg, DTYPES[d], OPS[op],
                       PRECISIONS[precision], _stream(x, stream), ctypes.byref(c)))
     return c.as_dict()

@@ -96,6 +96,18 @@ def tune_rows(torch, rows=64, cols=1 << 20):
     del x
 
 
+def tune_axis(torch):
+    """Axis reductions of the bench's 1 GiB shapes (middle axis of [16, 4096,
+    4096], first axis of [16384, 16384]), with the library's autotuner."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    x = torch.randn(16, 4096, 4096, generator=g, device="cuda")
+    for op in ("sum", "max", "min", "prod"):
+        cfg = pr.autotune("axis", x, op, dim=1)
+        print("axis [16,4096,4096] dim 1 f32 %s: %s" % (op, cfg), flush=True)
+    del x
+
+
 def main():
     import torch
     from . import synth
@@ -103,7 +115,7 @@ def main():
     ap.add_argument("--out", default=DEFAULT_PATH)
     ap.add_argument("--sizes", default="20,22,24,26,28,30")
     ap.add_argument("--quick", action="store_true", help="only 2^28 and the segmented workload")
-    ap.add_argument("--only", default="reduce,segmented,rows,backward",
+    ap.add_argument("--only", default="reduce,segmented,rows,backward,axis",
                     help="comma list of the parts to re-tune; the other entries of the shipped table are kept")
     args = ap.parse_args()
     parts = set(args.only.split(","))
@@ -145,6 +157,8 @@ def main():
         tune_rows(torch)
     if "backward" in parts:
         tune_backward(torch)
+    if "axis" in parts:
+        tune_axis(torch)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     pr.check(pr.pr_tune_save(args.out))
     print("saved", args.out)

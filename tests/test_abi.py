@@ -127,6 +127,15 @@ def test_axis_rejects(L):
     assert pr.pr_reduce_axis_backward(PROD, F32, None, 2, 4, 4, FAKE, None, FAKE, FAKE, None) == INVALID
     assert pr.pr_reduce_axis_backward(SUM, F32, None, 2, 4, -1, FAKE, None, None, FAKE, None) == INVALID
     assert pr.pr_reduce_axis_backward(SUM, F32, None, 2, 0, 4, None, None, None, None, None) == OK
+    best = pr.pr_config()
+    assert pr.pr_autotune_axis(None, 2, 4, 4, F32, SUM, PLAIN, None, ctypes.byref(best)) == INVALID
+    assert pr.pr_autotune_axis(FAKE, 2, 4, 1, F32, SUM, PLAIN, None, ctypes.byref(best)) == INVALID
+    assert pr.pr_autotune_axis(FAKE, 2, 4, 4, F32, AND, PLAIN, None, ctypes.byref(best)) == UNSUPPORTED
+    # the axis kind has its own configurations
+    c = pr.pr_config(64, 4, 2, 32)
+    assert pr.pr_set_config(4, F32, MAX, PLAIN, 1 << 20, ctypes.byref(c)) == OK
+    got = pr.pr_config()
+    assert pr.pr_get_config(4, F32, MAX, PLAIN, 1 << 20, ctypes.byref(got)) == OK and got.as_dict() == c.as_dict()
 
 
 def test_host_path_rejects(L):
