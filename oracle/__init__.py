@@ -77,6 +77,7 @@ def _L():
             "orc_prod_scaled": (I, [P, I64, I, PD, PI64]),
             "orc_prod_aux": (I, [P, I64, I, PD, PI64, PI64]),
             "orc_prod_except": (D, [P, I64, I, I64]),
+            "orc_scan": (I, [P, I64, I, I, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -249,6 +250,29 @@ def segmented_argext(x, offsets, dtype: str, op: str):
     a = _arr(x, dtype)
     off = np.asarray(offsets, dtype=np.int64)
     return [argext(a[int(off[s]):int(off[s + 1])], dtype, op) for s in range(off.size - 1)]
+
+
+# ---------------------------------------------------------------------------
+# Prefix scan
+# ---------------------------------------------------------------------------
+
+def scan(x, dtype: str, op: str, exclusive: bool = False):
+    """Prefix combinations of x in index order: y[i] = x[0] op ... op x[i]
+    (inclusive) or x[0] op ... op x[i-1] (exclusive, y[0] = identity).
+    Integer and bitwise combiners (y in the output type: int64 for an int32
+    sum) and float max / min (y as float64 values)."""
+    a = _arr(x, dtype)
+    n = a.size
+    if dtype in INT_DTYPES:
+        od = out_dtype(dtype, op)
+        y = np.zeros(n, dtype={"i64": np.int64, "i32": np.int32, "u32": np.uint32}[od])
+    else:
+        if op not in ("max", "min"):
+            raise ValueError("the float scan is defined for max and min")
+        y = np.zeros(n, dtype=np.float64)
+    if n and _L().orc_scan(_ptr(a), n, DTYPES[dtype], OPS[op], int(bool(exclusive)), _ptr(y)) != 0:
+        raise ValueError("bad combiner")
+    return y
 
 
 # ---------------------------------------------------------------------------

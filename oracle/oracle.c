@@ -29,6 +29,11 @@
  *                       product's gradient needs).
  *   orc_prod_except     prod_{j != i} x_j, the derivative of the product with
  *                       respect to x_i, straight from its definition.
+ *   orc_scan            the prefix combinations y_i = x_0 (x) ... (x) x_i
+ *                       (inclusive) or x_0 (x) ... (x) x_{i-1} (exclusive, y_0 the
+ *                       identity): Algorithm 1's loop, storing the accumulator
+ *                       after every step.  Integer/bitwise combiners and float
+ *                       max/min (the combiners whose result is exact).
  *
  * Build: gcc -std=c11 -O2 -ffp-contract=off -fPIC -shared (ISO C, no FMA
  * contraction, so that x86-64 and AArch64 hosts give identical results).
@@ -431,4 +436,68 @@ double orc_prod_except(const void* x, int64_t n, int dtype, int64_t skip) {
     if (zero) return neg ? -0.0 : 0.0;
     double r = dde_to_double(&a);
     return neg ? -r : r;
+}
+
+/* ------------------------------------------------------------------ */
+/* Prefix scan (exact combiners)                                       */
+/* ------------------------------------------------------------------ */
+
+/* One step of an integer combiner on 64-bit two's-complement bits; `sgn`
+ * selects signed order for max / min.  Sums and products wrap (the caller
+ * truncates to the output width). */
+static uint64_t int_step(uint64_t acc, uint64_t v, int op, int sgn) {
+    switch (op) {
+    case O_SUM: return acc + v;
+    case O_PROD: return acc * v;
+    case O_MAX: return sgn ? ((int64_t)v > (int64_t)acc ? v : acc) : (v > acc ? v : acc);
+    case O_MIN: return sgn ? ((int64_t)v < (int64_t)acc ? v : acc) : (v < acc ? v : acc);
+    case O_AND: return acc & v;
+    case O_OR: return acc | v;
+    default: return acc ^ v;
+    }
+}
+
+/* y: int64 per element for i32 SUM (the sum widens), else the input's own
+ * width for integers (two's complement); double values for float max/min. */
+int orc_scan(const void* x, int64_t n, int dtype, int op, int exclusive, void* y) {
+    if (dtype == O_I32 || dtype == O_U32 || dtype == O_I64) {
+        const int sgn = dtype != O_U32;
+        const int wide = dtype == O_I64 || (dtype == O_I32 && op == O_SUM);
+        uint64_t acc;
+        switch (op) {
+        case O_SUM: case O_OR: case O_XOR: acc = 0; break;
+        case O_PROD: acc = 1; break;
+        case O_AND: acc = ~0ull; break;
+        case O_MAX: acc = dtype == O_I64 ? (uint64_t)INT64_MIN : (dtype == O_I32 ? (uint64_t)(int64_t)INT32_MIN : 0); break;
+        case O_MIN: acc = dtype == O_I64 ? (uint64_t)INT64_MAX : (dtype == O_I32 ? (uint64_t)INT32_MAX : 0xffffffffull); break;
+        default: return -1;
+        }
+        for (int64_t i = 0; i < n; i++) {
+            uint64_t v;
+            if (dtype == O_I32) v = (uint64_t)(int64_t)((const int32_t*)x)[i];
+            else if (dtype == O_U32) v = ((const uint32_t*)x)[i];
+            else v = (uint64_t)((const int64_t*)x)[i];
+            if (exclusive) {
+                if (wide) ((uint64_t*)y)[i] = acc; else ((uint32_t*)y)[i] = (uint32_t)acc;
+            }
+            acc = int_step(acc, v, op, sgn);
+            if (!wide && dtype == O_I32 && (op == O_MAX || op == O_MIN)) acc = (uint64_t)(int64_t)(int32_t)acc;
+            if (!exclusive) {
+                if (wide) ((uint64_t*)y)[i] = acc; else ((uint32_t*)y)[i] = (uint32_t)acc;
+            }
+        }
+        return 0;
+    }
+    if (op != O_MAX && op != O_MIN) return -1;
+    double best = (op == O_MAX) ? -INFINITY : INFINITY;
+    for (int64_t i = 0; i < n; i++) {
+        const double v = elem_as_double(x, i, dtype);
+        if (exclusive) ((double*)y)[i] = best;
+        if (!isnan(best)) {
+            if (isnan(v)) best = v;                              /* NaN is final */
+            else if ((op == O_MAX) ? float_gt(v, best) : float_gt(best, v)) best = v;
+        }
+        if (!exclusive) ((double*)y)[i] = best;
+    }
+    return 0;
 }

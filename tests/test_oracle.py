@@ -395,6 +395,47 @@ def test_axis_oracle_matches_library_reductions(outer, n, inner):
     assert oracle.axis(xf, "f32", "sum", outer, n, inner) == [math.fsum(float(v) for v in c) for c in cols]
 
 
+@pytest.mark.parametrize("dtype,op", [("i32", "sum"), ("u32", "sum"), ("i64", "sum"), ("i32", "max"), ("i32", "min"),
+                                      ("u32", "max"), ("i64", "min"), ("u32", "xor"), ("i32", "and"), ("i64", "or"),
+                                      ("u32", "prod")])
+def test_scan_oracle_matches_library_prefixes(dtype, op):
+    """Prefix scans pinned to numpy's accumulate on exact integer data (sums and
+    products wrap in the output type), and to the reduction of each prefix."""
+    rng = np.random.default_rng(len(dtype) + len(op))
+    n = 1000
+    if dtype == "i32":
+        x = rng.integers(-2 ** 31, 2 ** 31, size=n).astype(np.int32)
+    elif dtype == "u32":
+        x = rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32)
+    else:
+        x = rng.integers(-2 ** 63, 2 ** 63 - 1, size=n, dtype=np.int64)
+    ufunc = {"sum": np.add, "max": np.maximum, "min": np.minimum, "xor": np.bitwise_xor, "and": np.bitwise_and,
+             "or": np.bitwise_or, "prod": np.multiply}[op]
+    wide = x.astype(np.int64) if (dtype == "i32" and op == "sum") else x
+    with np.errstate(over="ignore"):
+        want = ufunc.accumulate(wide, dtype=wide.dtype)
+    got = oracle.scan(x, dtype, op)
+    assert np.array_equal(got, want)
+    ex = oracle.scan(x, dtype, op, exclusive=True)
+    assert ex[0] == oracle.identity(dtype, op) and np.array_equal(ex[1:], want[:-1])
+    for i in (0, 1, 7, 500, n - 1):
+        assert int(got[i]) == oracle.reduce(x[:i + 1], dtype, op)
+
+
+def test_scan_oracle_float_extremes():
+    x = np.array([1.0, -0.0, 0.0, 3.0, np.nan, 5.0], dtype=np.float32)
+    assert list(oracle.scan(x, "f32", "max"))[:4] == [1.0, 1.0, 1.0, 3.0]
+    assert all(math.isnan(v) for v in oracle.scan(x, "f32", "max")[4:])
+    mn = oracle.scan(np.array([0.0, -0.0, 0.0], dtype=np.float32), "f32", "min")
+    assert [math.copysign(1.0, v) for v in mn] == [1.0, -1.0, -1.0]      # -0 < +0
+    ex = oracle.scan(x, "f32", "min", exclusive=True)
+    assert ex[0] == math.inf and ex[1] == 1.0
+    # every prefix's result is the reduction of that prefix
+    r = synth.normal_f32(300, 3)
+    got = oracle.scan(r, "f32", "max")
+    assert all(got[i] == oracle.reduce(r[:i + 1], "f32", "max") for i in range(300))
+
+
 def test_axis_oracle_empty_axis_and_rows():
     assert oracle.axis(np.zeros(0, np.float32), "f32", "max", 2, 0, 3) == [-math.inf] * 6
     assert oracle.axis(np.zeros(0, np.int32), "i32", "sum", 2, 0, 3) == [0] * 6
