@@ -193,6 +193,23 @@ pr_status pr_reduce_axis(const void* x, int64_t outer, int64_t n, int64_t inner,
                          pr_op op, pr_precision precision, void* out, int64_t* argidx,
                          pr_prod_aux* aux, pr_stream_t stream);
 
+/* Prefix scan in one pass (the prefix counterpart of Section 1.1's reduction;
+ * the paper names stream compaction and counting / radix sort as its users):
+ *   inclusive (exclusive == 0): y[i] = x[0] op x[1] op ... op x[i]
+ *   exclusive (exclusive != 0): y[0] = identity, y[i] = x[0] op ... op x[i-1]
+ * for the combiners whose result is exact: every integer / bitwise combiner
+ * (sums and products wrap in the output type, an I32 sum widens to I64 as in
+ * pr_out_dtype) and MAX / MIN of F32, F64, BF16 and F16 (NaN propagates,
+ * -0 < +0).  Float SUM / PROD: PR_ERR_UNSUPPORTED.  x: n elements, y: n
+ * elements of pr_out_dtype(dtype, op), device memory of the caller, not
+ * overlapping.  Bitwise deterministic.  Uses a per-stream tile-state buffer
+ * grown on first use (outside graph capture: PR_ERR_INVALID if a captured
+ * call would need to grow it).  Waits between tiles are bounded: one that
+ * runs out (not expected) leaves PR_ERR_TIMEOUT for pr_last_device_error and
+ * y unspecified. */
+pr_status pr_scan(const void* x, int64_t n, pr_dtype dtype, pr_op op, int32_t exclusive, void* y,
+                  pr_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Differentiation of a row reduction (F32 and F64)                         */
 /* ---------------------------------------------------------------------- */

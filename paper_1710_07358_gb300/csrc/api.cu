@@ -15,6 +15,7 @@
 #include "axis.cuh"
 #include "kernels.cuh"
 #include "registry.h"
+#include "scan.cuh"
 
 namespace pr {
 
@@ -49,6 +50,7 @@ void ensure_registered() {
         register_u32();
         register_i64();
         register_backward();
+        register_scan();
     });
 }
 
@@ -107,6 +109,8 @@ struct WsRec {
     size_t bytes;
     void* axis = nullptr;    // axis-reduction partials, grown on demand
     size_t axis_bytes = 0;
+    void* scan = nullptr;    // scan tile states + counters, grown on demand
+    size_t scan_tiles = 0;
 };
 static std::map<std::pair<int, cudaStream_t>, WsRec> g_ws;
 
@@ -506,6 +510,44 @@ static pr_status run_axis(const void* x, int64_t outer, int64_t n, int64_t inner
     return PR_OK;
 }
 
+// Scan state for (device, stream): `tiles` tile records and three counters
+// (next tile, blocks done, epoch).  Grown outside graph capture, zero-filled,
+// epoch 1, so that no stale flag can look current.
+static pr_status scan_state(cudaStream_t st, int64_t tiles, ScanTile** recs, unsigned** ctr) {
+    Workspace ws;
+    pr_status s = get_ws(st, &ws);
+    if (s != PR_OK) return s;
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    WsRec& w = g_ws[std::make_pair(dev, st)];
+    if ((int64_t)w.scan_tiles < tiles) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        PR_CUDA(cudaStreamIsCapturing(st, &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(PR_ERR_INVALID, "scan state for %lld tiles: run this size once before graph capture",
+                        (long long)tiles);
+        PR_CUDA(cudaStreamSynchronize(st));
+        if (w.scan) cudaFree(w.scan);
+        w.scan = nullptr;
+        w.scan_tiles = 0;
+        const int64_t grow = tiles < 4096 ? 4096 : tiles;
+        const size_t bytes = (size_t)grow * sizeof(ScanTile) + 64;
+        if (cudaMalloc(&w.scan, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PR_ERR_NOMEM, "scan state: allocation of %zu bytes failed", bytes);
+        }
+        PR_CUDA(cudaMemset(w.scan, 0, bytes));
+        const unsigned one = 1u;
+        PR_CUDA(cudaMemcpy(static_cast<char*>(w.scan) + (size_t)grow * sizeof(ScanTile) + 8, &one, 4,
+                           cudaMemcpyHostToDevice));
+        w.scan_tiles = (size_t)grow;
+    }
+    *recs = static_cast<ScanTile*>(w.scan);
+    *ctr = reinterpret_cast<unsigned*>(static_cast<char*>(w.scan) + w.scan_tiles * sizeof(ScanTile));
+    return PR_OK;
+}
+
 static pr_status run_axis_backward(int op, int dtype, const void* x, int64_t outer, int64_t n, int64_t inner,
                                    const void* g, const int64_t* argidx, const pr_prod_aux* aux, void* gi,
                                    cudaStream_t st) {
@@ -750,6 +792,46 @@ pr_status pr_reduce_axis_backward(pr_op op, pr_dtype dtype, const void* x, int64
     if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
     ensure_registered();
     return run_axis_backward(op, dtype, x, outer, n, inner, grad_out, argidx, aux, grad_in, (cudaStream_t)stream);
+}
+
+pr_status pr_scan(const void* x, int64_t n, pr_dtype dtype, pr_op op, int32_t exclusive, void* y,
+                  pr_stream_t stream) {
+    g_msg.clear();
+    if (!valid_dtype(dtype)) return fail(PR_ERR_INVALID, "unknown dtype %d", dtype);
+    if (!valid_op(op)) return fail(PR_ERR_INVALID, "unknown op %d", op);
+    if (is_float(dtype) && op != PR_MAX && op != PR_MIN)
+        return fail(PR_ERR_UNSUPPORTED, "float scans cover MAX and MIN (their results are exact)");
+    if (n < 0) return fail(PR_ERR_INVALID, "n must be >= 0");
+    if (n == 0) return PR_OK;
+    if (!x) return fail(PR_ERR_INVALID, "x is NULL");
+    if (!y) return fail(PR_ERR_INVALID, "y is NULL");
+    pr_status s;
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    if ((s = check_aligned(y, (int)pr_out_dtype(dtype, op), "y")) != PR_OK) return s;
+    ensure_registered();
+    cudaStream_t st = (cudaStream_t)stream;
+    const int es = elem_size(dtype);
+    const int64_t tile = (int64_t)kScanThreads * (kScanBytes / es);
+    const int64_t tiles = (n + tile - 1) / tile;
+    const bool vec = reinterpret_cast<uintptr_t>(x) % 32 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0;
+    const KernelEntry* e = reg_find(KernelKey{K_SCAN, (uint8_t)dtype, (uint8_t)op, 0, 0, 0, (uint8_t)(vec ? 1 : 0)});
+    if (!e) return fail(PR_ERR_UNSUPPORTED, "no scan kernel for dtype %d op %d", dtype, op);
+    DevInfo di;
+    if ((s = device_info(&di, nullptr)) != PR_OK) return s;
+    Workspace ws;
+    if ((s = get_ws(st, &ws)) != PR_OK) return s;
+    ScanTile* recs = nullptr;
+    unsigned* ctr = nullptr;
+    if ((s = scan_state(st, tiles, &recs, &ctr)) != PR_OK) return s;
+    int occ = 0;
+    if ((s = occupancy(e->fn, kScanThreads, &occ)) != PR_OK) return s;
+    if (occ < 1) return fail(PR_ERR_UNSUPPORTED, "scan kernel cannot run");
+    int64_t grid = (int64_t)di.sms * occ;
+    if (grid > tiles) grid = tiles;
+    ScanArgs a{x, y, n, tiles, exclusive ? 1 : 0, recs, ctr, ws.err};
+    cudaError_t err = reinterpret_cast<ScanLaunch>(e->launch)(a, (int)grid, kScanThreads, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "scan launch: %s", cudaGetErrorString(err));
+    return PR_OK;
 }
 
 pr_status pr_prepare(pr_stream_t stream) {

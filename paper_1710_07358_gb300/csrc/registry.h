@@ -13,11 +13,12 @@ struct SegArgs;
 struct RowArgs;
 struct AxisArgs;
 struct AxisBwdArgs;
+struct ScanArgs;
 struct BwdArgs;
 
 enum Kind : uint8_t {
     K_REDUCE = 0, K_SEGMENTED = 1, K_BACKWARD = 2, K_COMBINE = 3, K_ROWS = 4,
-    K_AXIS = 5, K_AXIS_FINISH = 6, K_AXIS_EMPTY = 7, K_AXIS_BACKWARD = 8
+    K_AXIS = 5, K_AXIS_FINISH = 6, K_AXIS_EMPTY = 7, K_AXIS_BACKWARD = 8, K_SCAN = 9
 };
 enum Aux : uint8_t { AUX_NONE = 0, AUX_ARG = 1, AUX_PROD = 2 };
 
@@ -31,6 +32,7 @@ using SegLaunch = cudaError_t (*)(const SegArgs&, int grid, int block, cudaStrea
 using RowLaunch = cudaError_t (*)(const RowArgs&, int grid, int block, cudaStream_t);
 using AxisLaunch = cudaError_t (*)(const AxisArgs&, int grid, int block, cudaStream_t);
 using AxisBwdLaunch = cudaError_t (*)(const AxisBwdArgs&, int grid, int block, cudaStream_t);
+using ScanLaunch = cudaError_t (*)(const ScanArgs&, int grid, int block, cudaStream_t);
 using BwdLaunch = cudaError_t (*)(const BwdArgs&, int grid, int block, cudaStream_t);
 using CombineLaunch = cudaError_t (*)(const char* parts, int count, void* out, int out_f64, cudaStream_t);
 
@@ -56,6 +58,7 @@ void register_i32();
 void register_u32();
 void register_i64();
 void register_backward();
+void register_scan();
 
 // Registers every family above exactly once (thread-safe).
 void ensure_registered();

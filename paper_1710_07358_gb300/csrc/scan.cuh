@@ -1,0 +1,32 @@
+// Layout shared by the scan kernel and the host: per-tile status records,
+// launch arguments and the tile shape.
+#pragma once
+#include <cstdint>
+
+namespace pr {
+
+// The aggregate and the inclusive prefix have their own words: a reader that
+// saw the aggregate flag must not pick up the inclusive value written later.
+struct ScanTile {
+    unsigned flag;              // (epoch << 2) | state: 1 aggregate, 2 inclusive prefix
+    unsigned pad;
+    unsigned long long agg;     // the tile's own combination (written before state 1)
+    unsigned long long incl;    // everything up to the tile's end (written before state 2)
+    unsigned long long pad2;
+};
+
+struct ScanArgs {
+    const void* x;
+    void* y;
+    int64_t n;
+    int64_t ntiles;
+    int exclusive;
+    ScanTile* tiles;
+    unsigned* ctr;              // [0] next tile, [1] blocks done, [2] epoch
+    int* err;
+};
+
+constexpr int kScanThreads = 256;
+constexpr int kScanBytes = 64;          // input bytes per thread and tile
+
+}  // namespace pr

@@ -56,6 +56,7 @@ _SIGS = {
     "pr_reduce_rows": [_P, _I64, _I64, _I, _I, _I, _P, _P, _P, _P],
     "pr_reduce_backward": [_I, _I, _P, _I64, _I64, _P, _P, _P, _P, _P],
     "pr_reduce_axis": [_P, _I64, _I64, _I64, _I, _I, _I, _P, _P, _P, _P],
+    "pr_scan": [_P, _I64, _I, _I, ctypes.c_int32, _P, _P],
     "pr_reduce_axis_backward": [_I, _I, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P],
     "pr_reduce_host": [_P, _I64, _I, _I, _P, _P],
     "pr_reduce_noalloc": [_P, _I64, _I, _I, _P, _P],
@@ -146,6 +147,10 @@ def pr_reduce_axis(x, outer, n, inner, dtype, op, precision, out, argidx, aux, s
 
 def pr_reduce_axis_backward(op, dtype, x, outer, n, inner, grad_out, argidx, aux, grad_in, stream):
     return lib().pr_reduce_axis_backward(op, dtype, x, outer, n, inner, grad_out, argidx, aux, grad_in, stream)
+
+
+def pr_scan(x, n, dtype, op, exclusive, y, stream):
+    return lib().pr_scan(x, n, dtype, op, exclusive, y, stream)
 
 
 def pr_reduce_host(host_x, n, dtype, op, host_out, stream):
@@ -323,6 +328,18 @@ def reduce_rows(x, op: str, precision: str = "plain", argidx: bool = False, aux:
     if aux:
         return out, ax
     return out
+
+
+def scan(x, op: str, exclusive: bool = False, out=None, stream=None):
+    """Prefix scan of a contiguous CUDA tensor (flattened) under op; same
+    number of elements, in the output type of the reduction (pr_out_dtype)."""
+    torch = _torch()
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("scan needs a contiguous CUDA tensor")
+    d = dtype_name(x)
+    y = out if out is not None else torch.empty(x.shape, dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
+    check(pr_scan(_ptr(x), x.numel(), DTYPES[d], OPS[op], 1 if exclusive else 0, _ptr(y), _stream(x, stream)))
+    return y
 
 
 def axis_shape(shape, dim):

@@ -138,6 +138,18 @@ def test_axis_rejects(L):
     assert pr.pr_get_config(4, F32, MAX, PLAIN, 1 << 20, ctypes.byref(got)) == OK and got.as_dict() == c.as_dict()
 
 
+def test_scan_rejects(L):
+    assert pr.pr_scan(FAKE, -1, I32, SUM, 0, FAKE, None) == INVALID
+    assert pr.pr_scan(None, 4, I32, SUM, 0, FAKE, None) == INVALID
+    assert pr.pr_scan(FAKE, 4, I32, SUM, 0, None, None) == INVALID
+    assert pr.pr_scan(FAKE, 4, F32, SUM, 0, FAKE, None) == UNSUPPORTED
+    assert pr.pr_scan(FAKE, 4, BF16, PROD, 1, FAKE, None) == UNSUPPORTED
+    assert pr.pr_scan(FAKE, 4, 99, SUM, 0, FAKE, None) == INVALID
+    assert pr.pr_scan(FAKE + 2, 4, I32, MAX, 0, FAKE, None) == INVALID
+    assert pr.pr_scan(FAKE, 4, I32, SUM, 0, FAKE + 4, None) == INVALID   # int64 output alignment
+    assert pr.pr_scan(None, 0, I32, SUM, 0, None, None) == OK
+
+
 def test_host_path_rejects(L):
     assert pr.pr_reduce_host(None, 5, F32, SUM, FAKE, None) == INVALID
     assert pr.pr_reduce_host(FAKE, 5, F32, SUM, None, None) == INVALID
