@@ -14,7 +14,8 @@ Also reported in the same line:
                segmented form (4096 log-uniform segments, autotuned, replayed from a
                CUDA graph), forward+backward of [64, 2^20] row reductions, and
                reductions of a non-last axis (1 GiB: middle axis of [16, 4096,
-               4096] with its gradient, first axis of [16384, 16384]).
+               4096] with its gradient, first axis of [16384, 16384]), and one-pass
+               prefix scans of 2^28 elements.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms]
 
@@ -167,7 +168,7 @@ def cpu_oracle_sum(x):
 # Secondary forms (all on the same GPU, same run)
 # --------------------------------------------------------------------------
 
-FORM_GROUPS = ("plain", "precision", "illcond", "segmented", "fwdbwd", "axis")
+FORM_GROUPS = ("plain", "precision", "illcond", "segmented", "fwdbwd", "axis", "scan")
 
 
 def forms(steps, warmup, peak, only=None, tune=True):
@@ -229,7 +230,41 @@ def forms(steps, warmup, peak, only=None, tune=True):
         fwdbwd(res, k, warmup, peak, st, g)
     if "axis" in want:
         axis(res, k, warmup, peak, st, g)
+    if "scan" in want:
+        scan(res, k, warmup, peak, st, g)
     return res
+
+
+def scan(res, k, warmup, peak, st, g):
+    """One-pass prefix scans of n = 2^28: uint32 sum (offsets of a counting
+    sort: 1 GiB read + 1 GiB written), int32 sum widening to int64 (1 GiB read,
+    2 GiB written) and fp32 running max (1 GiB + 1 GiB).  Bandwidth counts the
+    bytes read and written, like the copy that sets the measured peak."""
+    import torch
+    from paper_1710_07358_gb300 import pr
+    dev = torch.device("cuda")
+    n = 1 << 28
+    g.manual_seed(9)
+    xi = torch.randint(0, 1 << 8, (n,), generator=g, device=dev, dtype=torch.int32)
+    yu = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def put(name, per, nbytes):
+        res[name] = {"GB/s": round(gbs(nbytes, per), 1), "frac": round(gbs(nbytes, per) / peak, 4),
+                     "us": round(per * 1e3, 2)}
+
+    xu = xi.view(torch.uint32) if hasattr(torch, "uint32") else xi
+    _, per = time_launches(lambda: pr.check(pr.pr_scan(xu.data_ptr(), n, pr.DTYPES["u32"], pr.OPS["sum"], 1,
+                                                       yu.data_ptr(), st.cuda_stream)), k, warmup, st)
+    put("scan_u32_sum_exclusive", per, 2 * n * 4)
+    y64 = torch.empty(n, dtype=torch.int64, device=dev)
+    _, per = time_launches(lambda: pr.scan(xi, "sum", out=y64), k, warmup, st)
+    put("scan_i32_sum_to_i64", per, n * 4 + n * 8)
+    del y64, yu
+    xf = torch.randn(n, generator=g, device=dev)
+    yf = torch.empty_like(xf)
+    _, per = time_launches(lambda: pr.scan(xf, "max", out=yf), k, warmup, st)
+    put("scan_f32_max", per, 2 * n * 4)
+    del xf, yf, xi
 
 
 def axis(res, k, warmup, peak, st, g):

@@ -28,6 +28,7 @@
 namespace pr {
 
 constexpr int kScanSpin = 1 << 18;      // polls of one flag before giving up (each >= 64 ns)
+constexpr int kScanWin = 2;             // look-back step: kScanWin x 32 tiles
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -133,22 +134,85 @@ struct ScanMaxD {
 
 // ---- kernel --------------------------------------------------------------
 
-// Bounded wait for tile j's status in this launch's epoch; returns 1
-// (aggregate) or 2 (inclusive prefix).
-__device__ __forceinline__ unsigned scan_wait(const ScanTile* t, unsigned epoch, int* err) {
-    for (int it = 0; it < kScanSpin; it++) {
-        const unsigned f = ld_acquire_u32(&t->flag);
-        if ((f >> 2) == epoch && (f & 3u)) return f & 3u;
-        if (it >= 16) __nanosleep(64);
-    }
-    atomicOr(err, kErrTimeout);
-    return 2u;
-}
+// Tile status as the look-back sees it (state 1 aggregate, 2 inclusive).
+// Accumulators of at most 32 bits share one 64-bit word with the epoch and
+// the state, so one load reads a consistent (state, value) pair: a look-back
+// step costs one L2 round trip.  Wider accumulators use their own words
+// behind a release / acquire flag (two round trips).
+template <bool PACKED>
+struct TileStatus;
 
-__device__ __forceinline__ void scan_publish(ScanTile* t, unsigned long long v, unsigned epoch, unsigned state) {
-    st_relaxed_u64(state == 2u ? &t->incl : &t->agg, v);
-    st_release_u32(&t->flag, (epoch << 2) | state);
-}
+template <>
+struct TileStatus<true> {
+    __device__ __forceinline__ static unsigned long long* word(ScanTile* t) {
+        return reinterpret_cast<unsigned long long*>(&t->flag);
+    }
+    // low half: the flag in the same format as the two-word layout ((epoch <<
+    // 2) | state), so that neither layout mistakes the other's stale words for
+    // current ones; high half: the value
+    __device__ __forceinline__ static void publish(ScanTile* t, unsigned long long v, unsigned epoch, unsigned state) {
+        st_relaxed_u64(word(t), ((v & 0xffffffffull) << 32) | (unsigned long long)((epoch << 2) | state));
+    }
+    __device__ __forceinline__ static bool valid(unsigned long long w, unsigned epoch) {
+        const unsigned f = (unsigned)w;
+        return (f >> 2) == epoch && (f & 3u) != 0u;
+    }
+    // W tiles at once: the first loads all go out together; only tiles not
+    // yet published are polled again (bounded)
+    template <int W>
+    __device__ __forceinline__ static void read(ScanTile* const (&t)[W], const bool (&use)[W], unsigned epoch, int* err,
+                                                unsigned (&st)[W], unsigned long long (&v)[W]) {
+        unsigned long long w[W];
+#pragma unroll
+        for (int m = 0; m < W; m++) w[m] = use[m] ? ld_relaxed_u64(word(t[m])) : 0ull;
+#pragma unroll
+        for (int m = 0; m < W; m++) {
+            st[m] = 2u;
+            v[m] = 0ull;
+            if (!use[m]) continue;
+            int it = 0;
+            while (!valid(w[m], epoch) && it < kScanSpin) {
+                if (it >= 16) __nanosleep(64);
+                w[m] = ld_relaxed_u64(word(t[m]));
+                it++;
+            }
+            if (!valid(w[m], epoch)) atomicOr(err, kErrTimeout);
+            else st[m] = (unsigned)w[m] & 3u;
+            v[m] = w[m] >> 32;
+        }
+    }
+};
+
+template <>
+struct TileStatus<false> {
+    __device__ __forceinline__ static void publish(ScanTile* t, unsigned long long v, unsigned epoch, unsigned state) {
+        st_relaxed_u64(state == 2u ? &t->incl : &t->agg, v);
+        st_release_u32(&t->flag, (epoch << 2) | state);
+    }
+    template <int W>
+    __device__ __forceinline__ static void read(ScanTile* const (&t)[W], const bool (&use)[W], unsigned epoch, int* err,
+                                                unsigned (&st)[W], unsigned long long (&v)[W]) {
+#pragma unroll
+        for (int m = 0; m < W; m++) {
+            st[m] = 2u;
+            v[m] = 0ull;
+            if (!use[m]) continue;
+            unsigned f = 0;
+            int it = 0;
+            for (; it < kScanSpin; it++) {
+                f = ld_acquire_u32(&t[m]->flag);
+                if ((f >> 2) == epoch && (f & 3u)) break;
+                if (it >= 16) __nanosleep(64);
+            }
+            if (it == kScanSpin) {
+                atomicOr(err, kErrTimeout);
+            } else {
+                st[m] = f & 3u;
+                v[m] = ld_relaxed_u64(st[m] == 2u ? &t[m]->incl : &t[m]->agg);
+            }
+        }
+    }
+};
 
 template <class Op>
 __device__ __forceinline__ typename Op::A warp_all(typename Op::A v) {
@@ -170,6 +234,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs a) {
     const In* x = static_cast<const In*>(a.x);
     Out* y = static_cast<Out*>(a.y);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    using Status = TileStatus<(sizeof(A) <= 4)>;
 
     __shared__ int64_t s_tile;
     __shared__ unsigned s_epoch;
@@ -229,23 +294,36 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs a) {
         if (warp == 0) {
             A pre = Op::ident();
             if (t == 0) {
-                if (lane == 0) scan_publish(a.tiles, Op::pack(agg), epoch, 2u);
+                if (lane == 0) Status::publish(a.tiles, Op::pack(agg), epoch, 2u);
             } else {
-                if (lane == 0) scan_publish(a.tiles + t, Op::pack(agg), epoch, 1u);
-                for (int64_t base = t - 1;; base -= 32) {
-                    const int64_t j = base - lane;
-                    unsigned st = 2u;
-                    A v = Op::ident();
-                    if (j >= 0) {
-                        st = scan_wait(a.tiles + j, epoch, a.err);
-                        v = Op::unpack(ld_relaxed_u64(st == 2u ? &a.tiles[j].incl : &a.tiles[j].agg));
+                if (lane == 0) Status::publish(a.tiles + t, Op::pack(agg), epoch, 1u);
+                // windows of kScanWin x 32 predecessors: lane k reads tiles
+                // base - k - 32 m; sub-windows are taken nearest first
+                for (int64_t base = t - 1;; base -= 32 * kScanWin) {
+                    ScanTile* tp[kScanWin];
+                    bool use[kScanWin];
+#pragma unroll
+                    for (int m = 0; m < kScanWin; m++) {
+                        const int64_t j = base - lane - 32 * m;
+                        use[m] = j >= 0;
+                        tp[m] = a.tiles + (j >= 0 ? j : 0);
                     }
-                    const unsigned incl = __ballot_sync(0xffffffffu, st == 2u);
-                    const int stop = incl ? __ffs(incl) - 1 : 31;
-                    pre = Op::comb(pre, warp_all<Op>(lane <= stop ? v : Op::ident()));
-                    if (incl) break;
+                    unsigned st[kScanWin];
+                    unsigned long long vb[kScanWin];
+                    Status::template read<kScanWin>(tp, use, epoch, a.err, st, vb);
+                    bool found = false;
+#pragma unroll
+                    for (int m = 0; m < kScanWin; m++) {
+                        if (found) break;
+                        const A v = use[m] ? Op::unpack(vb[m]) : Op::ident();
+                        const unsigned incl = __ballot_sync(0xffffffffu, st[m] == 2u);
+                        const int stop = incl ? __ffs(incl) - 1 : 31;
+                        pre = Op::comb(pre, warp_all<Op>(lane <= stop ? v : Op::ident()));
+                        found = incl != 0u;
+                    }
+                    if (found) break;
                 }
-                if (lane == 0) scan_publish(a.tiles + t, Op::pack(Op::comb(pre, agg)), epoch, 2u);
+                if (lane == 0) Status::publish(a.tiles + t, Op::pack(Op::comb(pre, agg)), epoch, 2u);
             }
             if (lane == 0) s_prefix = pre;
         }

@@ -7,6 +7,8 @@ namespace pr {
 
 // The aggregate and the inclusive prefix have their own words: a reader that
 // saw the aggregate flag must not pick up the inclusive value written later.
+// Accumulators of at most 32 bits instead travel with the flag in one 64-bit
+// word (flag in the low half, value in the high half).
 struct ScanTile {
     unsigned flag;              // (epoch << 2) | state: 1 aggregate, 2 inclusive prefix
     unsigned pad;
