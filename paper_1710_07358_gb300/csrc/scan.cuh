@@ -28,7 +28,12 @@ struct ScanArgs {
     int* err;
 };
 
+// Tiles of 256 x 128 input bytes (32 KB).  A block serialises claim, load,
+// look-back and stores per tile, and the look-back frontier must keep up with
+// the tiles HBM streams in, so tiles are large and several blocks share an SM
+// (measured on GB300, 2^28 uint32 prefix sums: 16 KB tiles 601 us, 32 KB tiles
+// 544 us, 64 KB tiles 661 us).
 constexpr int kScanThreads = 256;
-constexpr int kScanBytes = 64;          // input bytes per thread and tile
+constexpr int kScanBytes = 128;         // input bytes per thread and tile
 
 }  // namespace pr
