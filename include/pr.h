@@ -210,6 +210,13 @@ pr_status pr_reduce_axis(const void* x, int64_t outer, int64_t n, int64_t inner,
 pr_status pr_scan(const void* x, int64_t n, pr_dtype dtype, pr_op op, int32_t exclusive, void* y,
                   pr_stream_t stream);
 
+/* Self-check of the bounded waits pr_scan relies on: enqueues one wait, of
+ * `polls` polls (>= 1; each at least 64 ns after the first 16), on a tile
+ * state that nothing publishes.  The wait gives up and sets PR_ERR_TIMEOUT in
+ * the stream's device error word (read it with pr_last_device_error); the
+ * context stays usable. */
+pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Differentiation of a row reduction (F32 and F64)                         */
 /* ---------------------------------------------------------------------- */

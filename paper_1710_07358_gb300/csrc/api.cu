@@ -834,6 +834,22 @@ pr_status pr_scan(const void* x, int64_t n, pr_dtype dtype, pr_op op, int32_t ex
     return PR_OK;
 }
 
+pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream) {
+    g_msg.clear();
+    if (polls < 1) return fail(PR_ERR_INVALID, "polls must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace ws;
+    pr_status s = get_ws(st, &ws);
+    if (s != PR_OK) return s;
+    ScanTile* rec = nullptr;
+    PR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&rec), sizeof(ScanTile), st));
+    PR_CUDA(cudaMemsetAsync(rec, 0, sizeof(ScanTile), st));
+    cudaError_t err = launch_wait_probe(rec, polls, ws.err, st);
+    cudaFreeAsync(rec, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "wait probe launch: %s", cudaGetErrorString(err));
+    return PR_OK;
+}
+
 pr_status pr_prepare(pr_stream_t stream) {
     g_msg.clear();
     ensure_registered();

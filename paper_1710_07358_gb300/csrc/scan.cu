@@ -161,7 +161,7 @@ struct TileStatus<true> {
     // yet published are polled again (bounded)
     template <int W>
     __device__ __forceinline__ static void read(ScanTile* const (&t)[W], const bool (&use)[W], unsigned epoch, int* err,
-                                                unsigned (&st)[W], unsigned long long (&v)[W]) {
+                                                unsigned (&st)[W], unsigned long long (&v)[W], int spin = kScanSpin) {
         unsigned long long w[W];
 #pragma unroll
         for (int m = 0; m < W; m++) w[m] = use[m] ? ld_relaxed_u64(word(t[m])) : 0ull;
@@ -171,7 +171,7 @@ struct TileStatus<true> {
             v[m] = 0ull;
             if (!use[m]) continue;
             int it = 0;
-            while (!valid(w[m], epoch) && it < kScanSpin) {
+            while (!valid(w[m], epoch) && it < spin) {
                 if (it >= 16) __nanosleep(64);
                 w[m] = ld_relaxed_u64(word(t[m]));
                 it++;
@@ -191,7 +191,7 @@ struct TileStatus<false> {
     }
     template <int W>
     __device__ __forceinline__ static void read(ScanTile* const (&t)[W], const bool (&use)[W], unsigned epoch, int* err,
-                                                unsigned (&st)[W], unsigned long long (&v)[W]) {
+                                                unsigned (&st)[W], unsigned long long (&v)[W], int spin = kScanSpin) {
 #pragma unroll
         for (int m = 0; m < W; m++) {
             st[m] = 2u;
@@ -199,12 +199,12 @@ struct TileStatus<false> {
             if (!use[m]) continue;
             unsigned f = 0;
             int it = 0;
-            for (; it < kScanSpin; it++) {
+            for (; it < spin; it++) {
                 f = ld_acquire_u32(&t[m]->flag);
                 if ((f >> 2) == epoch && (f & 3u)) break;
                 if (it >= 16) __nanosleep(64);
             }
-            if (it == kScanSpin) {
+            if (it == spin) {
                 atomicOr(err, kErrTimeout);
             } else {
                 st[m] = f & 3u;
@@ -362,6 +362,24 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs a) {
             st_release_u32(a.ctr + 2, ne == 0u ? 1u : ne);
         }
     }
+}
+
+// Self-check of the bounded wait: one thread waits, with `spin` polls, on a
+// tile state that nothing publishes; the wait must give up and set
+// kErrTimeout in the error word.
+__global__ void k_wait_probe(ScanTile* t, int spin, int* err) {
+    if (threadIdx.x != 0) return;
+    ScanTile* tp[1] = {t};
+    const bool use[1] = {true};
+    unsigned st[1];
+    unsigned long long v[1];
+    TileStatus<true>::read<1>(tp, use, 1u, err, st, v, spin);
+    TileStatus<false>::read<1>(tp, use, 1u, err, st, v, spin);
+}
+
+cudaError_t launch_wait_probe(ScanTile* t, int spin, int* err, cudaStream_t st) {
+    k_wait_probe<<<1, 32, 0, st>>>(t, spin, err);
+    return cudaGetLastError();
 }
 
 template <class Op, bool VEC>

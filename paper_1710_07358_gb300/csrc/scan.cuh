@@ -2,6 +2,7 @@
 // launch arguments and the tile shape.
 #pragma once
 #include <cstdint>
+#include <cuda_runtime.h>
 
 namespace pr {
 
@@ -35,5 +36,8 @@ struct ScanArgs {
 // 544 us, 64 KB tiles 661 us).
 constexpr int kScanThreads = 256;
 constexpr int kScanBytes = 128;         // input bytes per thread and tile
+
+// One bounded wait on a tile state nothing publishes (zero-filled, epoch 1).
+cudaError_t launch_wait_probe(ScanTile* t, int spin, int* err, cudaStream_t st);
 
 }  // namespace pr

@@ -57,6 +57,7 @@ _SIGS = {
     "pr_reduce_backward": [_I, _I, _P, _I64, _I64, _P, _P, _P, _P, _P],
     "pr_reduce_axis": [_P, _I64, _I64, _I64, _I, _I, _I, _P, _P, _P, _P],
     "pr_scan": [_P, _I64, _I, _I, ctypes.c_int32, _P, _P],
+    "pr_check_bounded_wait": [ctypes.c_int32, _P],
     "pr_reduce_axis_backward": [_I, _I, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P],
     "pr_reduce_host": [_P, _I64, _I, _I, _P, _P],
     "pr_reduce_noalloc": [_P, _I64, _I, _I, _P, _P],
@@ -151,6 +152,10 @@ def pr_reduce_axis_backward(op, dtype, x, outer, n, inner, grad_out, argidx, aux
 
 def pr_scan(x, n, dtype, op, exclusive, y, stream):
     return lib().pr_scan(x, n, dtype, op, exclusive, y, stream)
+
+
+def pr_check_bounded_wait(polls, stream):
+    return lib().pr_check_bounded_wait(polls, stream)
 
 
 def pr_reduce_host(host_x, n, dtype, op, host_out, stream):

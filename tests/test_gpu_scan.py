@@ -139,3 +139,16 @@ def test_scan_rejects():
     x = torch.zeros(16, dtype=torch.float32, device="cuda")
     with pytest.raises(pr.PrError):
         pr.scan(x, "sum")
+
+
+def test_bounded_wait_runs_out_and_reports_timeout():
+    """The look-back's bounded wait, on a tile state nothing publishes: it must
+    give up, leave PR_ERR_TIMEOUT in the error word, and leave the context
+    usable (a scan right after is correct)."""
+    import torch
+    assert pr.last_device_error() == 0
+    pr.check(pr.pr_check_bounded_wait(2000, torch.cuda.current_stream().cuda_stream))
+    assert pr.last_device_error() == 4                       # PR_ERR_TIMEOUT
+    assert pr.last_device_error() == 0                       # read and cleared
+    x = gen("i32", 100000, 8)
+    assert_same(run(x, "i32", "sum", False), oracle.scan(x, "i32", "sum"), "i32")
