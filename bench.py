@@ -236,14 +236,14 @@ def forms(steps, warmup, peak, only=None, tune=True):
 
 
 def scan(res, k, warmup, peak, st, g):
-    """One-pass prefix scans of n = 2^28: uint32 sum (offsets of a counting
+    """One-pass prefix scans of n = 2^28 (or the --n-log2 size): uint32 sum (offsets of a counting
     sort: 1 GiB read + 1 GiB written), int32 sum widening to int64 (1 GiB read,
     2 GiB written) and fp32 running max (1 GiB + 1 GiB).  Bandwidth counts the
     bytes read and written, like the copy that sets the measured peak."""
     import torch
     from paper_1710_07358_gb300 import pr
     dev = torch.device("cuda")
-    n = 1 << 28
+    n = N_HEAD                  # 2^28 unless --n-log2 asks for a profiling case
     g.manual_seed(9)
     xi = torch.randint(0, 1 << 8, (n,), generator=g, device=dev, dtype=torch.int32)
     yu = torch.empty(n, dtype=torch.int32, device=dev)
