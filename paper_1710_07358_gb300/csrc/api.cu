@@ -502,7 +502,8 @@ static pr_status run_axis(const void* x, int64_t outer, int64_t n, int64_t inner
         const KernelEntry* f = reg_find(KernelKey{K_AXIS_FINISH, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec,
                                                   (uint8_t)aux, 0, 0});
         if (!f) return fail(PR_ERR_UNSUPPORTED, "no axis finishing kernel");
-        const int64_t fgrid = (outer * inner * 32 + 255) / 256;
+        const int64_t per_out = a.splits <= kAxisThreadFinish ? 1 : 32;   // threads per output
+        const int64_t fgrid = (outer * inner * per_out + 255) / 256;
         if (fgrid > 0x7fffffff) return fail(PR_ERR_INVALID, "axis reduction too large for one launch");
         err = reinterpret_cast<AxisLaunch>(f->launch)(a, (int)fgrid, 256, st);
         if (err != cudaSuccess) return fail(PR_ERR_CUDA, "axis finish launch: %s", cudaGetErrorString(err));

@@ -13,8 +13,9 @@
 //   column then combine by an xor butterfly over the row bits of the lane
 //   index, in a fixed order.  With one split the warp writes the outputs; with
 //   more, it writes its partials, and k_axis_finish combines each output's
-//   partials in split order (one warp per output, a fixed tree), so results
-//   are deterministic for a fixed launch shape.
+//   partials in a fixed order (one thread per output folding the splits in
+//   order, or with many splits one warp per output and a fixed tree), so
+//   results are deterministic for a fixed launch shape.
 // k_axis_backward  gradient of an axis reduction: grad_in[p, i, q] from
 //   grad_out[p, q] and the per-output state, one streaming write.
 #pragma once
@@ -34,8 +35,13 @@ struct AxisArgs {
     int64_t* argidx;
     pr_prod_aux* aux;
     int out_f64;
-    char* scratch;            // splits > 1: partials [p][q][split] of GridR<T>::Part
+    char* scratch;            // splits > 1: partials of GridR<T>::Part, [split][output] when
+                              // splits <= kAxisThreadFinish, else [output][split]
 };
+
+// Up to this many splits the finishing pass takes one thread per output
+// (coalesced over outputs); beyond it, one warp per output.
+constexpr int kAxisThreadFinish = 64;
 
 // A column's elements reach its accumulator in increasing index order, so a
 // trait may take them with a cheaper in-order step (add_ordered).
@@ -118,22 +124,35 @@ __global__ void __launch_bounds__(MaxBlock<T>::value) k_axis(AxisArgs a) {
                 GR::store(a.out, o, g, f64);
                 GR::store_aux(a.argidx, a.aux, o, g, 0);
             } else {
-                reinterpret_cast<G*>(a.scratch)[o * a.splits + s] = g;
+                const int64_t nout = a.outer * a.inner;
+                reinterpret_cast<G*>(a.scratch)[a.splits <= kAxisThreadFinish ? s * nout + o : o * a.splits + s] = g;
             }
         }
     }
 }
 
-// One warp per output: the lanes take the splits in order (lane, lane + 32,
-// ...) and combine by a fixed butterfly.
+// Few splits: one thread per output folds its splits in order.  Many: one
+// warp per output, the lanes taking the splits in order (lane, lane + 32, ...)
+// and combining by a fixed butterfly.
 template <class T>
 __global__ void __launch_bounds__(256) k_axis_finish(AxisArgs a) {
     using GR = GridR<T>;
     using G = typename GR::Part;
+    const int64_t nout = a.outer * a.inner;
+    const G* part = reinterpret_cast<const G*>(a.scratch);
+    if (a.splits <= kAxisThreadFinish) {
+        const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (o >= nout) return;
+        G q = part[o];
+        for (int64_t s = 1; s < a.splits; s++) q = GR::combine(q, part[s * nout + o]);
+        GR::store(a.out, o, q, a.out_f64 != 0);
+        GR::store_aux(a.argidx, a.aux, o, q, 0);
+        return;
+    }
     const int lane = threadIdx.x & 31;
     const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (o >= a.outer * a.inner) return;
-    const G* src = reinterpret_cast<const G*>(a.scratch) + o * a.splits;
+    if (o >= nout) return;
+    const G* src = part + o * a.splits;
     G q = GR::part_init();
     for (int64_t s = lane; s < a.splits; s += 32) q = GR::combine(q, src[s]);
     q = GR::warp_reduce(q);
