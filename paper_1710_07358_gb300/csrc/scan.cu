@@ -137,8 +137,8 @@ struct ScanMaxD {
 // Tile status as the look-back sees it (state 1 aggregate, 2 inclusive).
 // Accumulators of at most 32 bits share one 64-bit word with the epoch and
 // the state, so one load reads a consistent (state, value) pair: a look-back
-// step costs one L2 round trip.  Wider accumulators use their own words
-// behind a release / acquire flag (two round trips).
+// step costs one L2 round trip.  Wider accumulators share a 16-byte word with
+// them, read and written by 128-bit atomics (also one round trip).
 template <bool PACKED>
 struct TileStatus;
 
@@ -183,36 +183,62 @@ struct TileStatus<true> {
     }
 };
 
+// 64-bit accumulators: flag and value in one 16-byte word, written and read
+// with 128-bit atomics (exchange; compare-and-swap with a comparand that a
+// published word never equals, which returns the word unchanged), so a step
+// is still one round trip.
+__device__ __forceinline__ void exch128(ScanTile* t, unsigned long long lo, unsigned long long hi) {
+    asm volatile("{\n\t.reg .b128 d, b;\n\t"
+                 "mov.b128 b, {%0, %1};\n\t"
+                 "atom.relaxed.gpu.global.exch.b128 d, [%2], b;\n\t}"
+                 :: "l"(lo), "l"(hi), "l"(&t->flag) : "memory");
+}
+__device__ __forceinline__ void read128(ScanTile* t, unsigned long long& lo, unsigned long long& hi) {
+    asm volatile("{\n\t.reg .b128 d, z;\n\t"
+                 "mov.b128 z, {%2, %2};\n\t"
+                 "atom.relaxed.gpu.global.cas.b128 d, [%3], z, z;\n\t"
+                 "mov.b128 {%0, %1}, d;\n\t}"
+                 : "=l"(lo), "=l"(hi) : "l"(0ull), "l"(&t->flag) : "memory");
+}
+
 template <>
 struct TileStatus<false> {
+    // low word: the flag ((epoch << 2) | state, as in the other layout); high word: the value
     __device__ __forceinline__ static void publish(ScanTile* t, unsigned long long v, unsigned epoch, unsigned state) {
-        st_relaxed_u64(state == 2u ? &t->incl : &t->agg, v);
-        st_release_u32(&t->flag, (epoch << 2) | state);
+        exch128(t, (unsigned long long)((epoch << 2) | state), v);
+    }
+    __device__ __forceinline__ static bool valid(unsigned long long lo, unsigned epoch) {
+        const unsigned f = (unsigned)lo;
+        return (f >> 2) == epoch && (f & 3u) != 0u;
     }
     template <int W>
     __device__ __forceinline__ static void read(ScanTile* const (&t)[W], const bool (&use)[W], unsigned epoch, int* err,
                                                 unsigned (&st)[W], unsigned long long (&v)[W], int spin = kScanSpin) {
+        unsigned long long lo[W], hi[W];
+#pragma unroll
+        for (int m = 0; m < W; m++) {
+            lo[m] = 0ull;
+            hi[m] = 0ull;
+            if (use[m]) read128(t[m], lo[m], hi[m]);
+        }
 #pragma unroll
         for (int m = 0; m < W; m++) {
             st[m] = 2u;
             v[m] = 0ull;
             if (!use[m]) continue;
-            unsigned f = 0;
             int it = 0;
-            for (; it < spin; it++) {
-                f = ld_acquire_u32(&t[m]->flag);
-                if ((f >> 2) == epoch && (f & 3u)) break;
+            while (!valid(lo[m], epoch) && it < spin) {
                 if (it >= 16) __nanosleep(64);
+                read128(t[m], lo[m], hi[m]);
+                it++;
             }
-            if (it == spin) {
-                atomicOr(err, kErrTimeout);
-            } else {
-                st[m] = f & 3u;
-                v[m] = ld_relaxed_u64(st[m] == 2u ? &t[m]->incl : &t[m]->agg);
-            }
+            if (!valid(lo[m], epoch)) atomicOr(err, kErrTimeout);
+            else st[m] = (unsigned)lo[m] & 3u;
+            v[m] = hi[m];
         }
     }
 };
+
 
 template <class Op>
 __device__ __forceinline__ typename Op::A warp_all(typename Op::A v) {

@@ -6,16 +6,16 @@
 
 namespace pr {
 
-// The aggregate and the inclusive prefix have their own words: a reader that
-// saw the aggregate flag must not pick up the inclusive value written later.
-// Accumulators of at most 32 bits instead travel with the flag in one 64-bit
-// word (flag in the low half, value in the high half).
-struct ScanTile {
-    unsigned flag;              // (epoch << 2) | state: 1 aggregate, 2 inclusive prefix
-    unsigned pad;
-    unsigned long long agg;     // the tile's own combination (written before state 1)
-    unsigned long long incl;    // everything up to the tile's end (written before state 2)
-    unsigned long long pad2;
+// One tile's status: the flag ((epoch << 2) | state: 1 aggregate, 2 inclusive
+// prefix) travels with its value in one word that is written and read whole,
+// so a reader never pairs a flag with a value from another state.
+// Accumulators of at most 32 bits: the 64-bit word {flag, value}; 64-bit
+// accumulators: the 16-byte word {flag, pad, value} (128-bit atomics).
+struct alignas(32) ScanTile {
+    unsigned flag;
+    unsigned value32;
+    unsigned long long value64;
+    unsigned long long pad[2];
 };
 
 struct ScanArgs {
