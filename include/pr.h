@@ -204,16 +204,20 @@ pr_status pr_reduce_axis(const void* x, int64_t outer, int64_t n, int64_t inner,
  * elements of pr_out_dtype(dtype, op), device memory of the caller, not
  * overlapping.  Bitwise deterministic.  Uses a per-stream tile-state buffer
  * grown on first use (outside graph capture: PR_ERR_INVALID if a captured
- * call would need to grow it).  Waits between tiles are bounded: one that
- * runs out (not expected) leaves PR_ERR_TIMEOUT for pr_last_device_error and
- * y unspecified. */
+ * call would need to grow it).  Every wait is bounded (tile states: 2^18
+ * polls; shared-memory barriers: 250 ms): one that runs out (not expected)
+ * leaves PR_ERR_TIMEOUT for pr_last_device_error and y unspecified.
+ * Alignment: x and y 16-byte aligned take the staged path (bulk copies into
+ * shared memory); otherwise every tile is read from x directly. */
 pr_status pr_scan(const void* x, int64_t n, pr_dtype dtype, pr_op op, int32_t exclusive, void* y,
                   pr_stream_t stream);
 
-/* Self-check of the bounded waits pr_scan relies on: enqueues one wait, of
- * `polls` polls (>= 1; each at least 64 ns after the first 16), on a tile
- * state that nothing publishes.  The wait gives up and sets PR_ERR_TIMEOUT in
- * the stream's device error word (read it with pr_last_device_error); the
+/* Self-check of the bounded waits pr_scan relies on: enqueues, in one
+ * thread, a wait of `polls` polls (>= 1; each at least 64 ns after the first
+ * 16) on a tile state that nothing publishes (in both status layouts), then
+ * a wait of `polls` microseconds on a shared-memory barrier phase that
+ * nothing completes.  Each wait gives up and sets PR_ERR_TIMEOUT in the
+ * stream's device error word (read it with pr_last_device_error); the
  * context stays usable. */
 pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream);
 

@@ -215,15 +215,22 @@ static pr_config lookup_cfg(int kind, int dtype, int op, int prec, int64_t n) {
     return it != g_tuned.end() ? it->second : default_cfg(kind, dtype, op, prec);
 }
 
-static std::map<std::pair<const void*, int>, int> g_occ;
+static std::map<std::tuple<int, const void*, int>, int> g_occ;
 
-static pr_status occupancy(const void* fn, int block, int* bps) {
+// Resident blocks per SM of `fn` at `block` threads and `smem` bytes of
+// dynamic shared memory (allowed above the 48 KB default on first use), per
+// device.
+static pr_status occupancy(const void* fn, int block, int* bps, size_t smem = 0) {
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_mu);
-    auto key = std::make_pair(fn, block);
+    auto key = std::make_tuple(dev, fn, block);
     auto it = g_occ.find(key);
     if (it == g_occ.end()) {
+        if (smem > 48 * 1024)
+            PR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int nb = 0;
-        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0));
+        PR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem));
         it = g_occ.emplace(key, nb).first;
     }
     *bps = it->second;
@@ -812,9 +819,10 @@ pr_status pr_scan(const void* x, int64_t n, pr_dtype dtype, pr_op op, int32_t ex
     ensure_registered();
     cudaStream_t st = (cudaStream_t)stream;
     const int es = elem_size(dtype);
-    const int64_t tile = (int64_t)kScanThreads * (kScanBytes / es);
+    const int64_t tile = kScanTileBytes / es;
     const int64_t tiles = (n + tile - 1) / tile;
-    const bool vec = reinterpret_cast<uintptr_t>(x) % 32 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0;
+    if (tiles > (int64_t)1 << 31) return fail(PR_ERR_INVALID, "scan of %lld elements: too many tiles", (long long)n);
+    const bool vec = reinterpret_cast<uintptr_t>(x) % 16 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0;
     const KernelEntry* e = reg_find(KernelKey{K_SCAN, (uint8_t)dtype, (uint8_t)op, 0, 0, 0, (uint8_t)(vec ? 1 : 0)});
     if (!e) return fail(PR_ERR_UNSUPPORTED, "no scan kernel for dtype %d op %d", dtype, op);
     DevInfo di;
@@ -825,12 +833,13 @@ pr_status pr_scan(const void* x, int64_t n, pr_dtype dtype, pr_op op, int32_t ex
     unsigned* ctr = nullptr;
     if ((s = scan_state(st, tiles, &recs, &ctr)) != PR_OK) return s;
     int occ = 0;
-    if ((s = occupancy(e->fn, kScanThreads, &occ)) != PR_OK) return s;
+    const size_t smem = (size_t)kScanStages * kScanTileBytes;
+    if ((s = occupancy(e->fn, kScanThreads, &occ, smem)) != PR_OK) return s;
     if (occ < 1) return fail(PR_ERR_UNSUPPORTED, "scan kernel cannot run");
     int64_t grid = (int64_t)di.sms * occ;
     if (grid > tiles) grid = tiles;
     ScanArgs a{x, y, n, tiles, exclusive ? 1 : 0, recs, ctr, ws.err};
-    cudaError_t err = reinterpret_cast<ScanLaunch>(e->launch)(a, (int)grid, kScanThreads, st);
+    cudaError_t err = reinterpret_cast<ScanLaunch>(e->launch)(a, (int)grid, kScanThreads, smem, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "scan launch: %s", cudaGetErrorString(err));
     return PR_OK;
 }

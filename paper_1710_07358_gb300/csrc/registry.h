@@ -32,7 +32,7 @@ using SegLaunch = cudaError_t (*)(const SegArgs&, int grid, int block, cudaStrea
 using RowLaunch = cudaError_t (*)(const RowArgs&, int grid, int block, cudaStream_t);
 using AxisLaunch = cudaError_t (*)(const AxisArgs&, int grid, int block, cudaStream_t);
 using AxisBwdLaunch = cudaError_t (*)(const AxisBwdArgs&, int grid, int block, cudaStream_t);
-using ScanLaunch = cudaError_t (*)(const ScanArgs&, int grid, int block, cudaStream_t);
+using ScanLaunch = cudaError_t (*)(const ScanArgs&, int grid, int block, size_t smem, cudaStream_t);
 using BwdLaunch = cudaError_t (*)(const BwdArgs&, int grid, int block, cudaStream_t);
 using CombineLaunch = cudaError_t (*)(const char* parts, int count, void* out, int out_f64, cudaStream_t);
 

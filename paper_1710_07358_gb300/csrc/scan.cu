@@ -4,21 +4,25 @@
 // the reduction (Section 1.1), whose consumers the paper names (stream
 // compaction, counting and radix sort).
 //
-// k_scan  persistent blocks claim tiles in order from an atomic counter, so a
-// block only ever waits for tiles that running blocks hold.  Per tile: each
-// thread scans its 64 bytes of input, the block scans the thread totals
-// (shuffles, then one value per warp), the block publishes the tile's
-// aggregate, and warp 0 looks back over the preceding tiles, 32 at a time:
-// tiles that already know their inclusive prefix end the walk, the others
-// contribute their aggregates (decoupled look-back).  The tile then publishes
-// its inclusive prefix and writes its outputs.  The combiners are exact,
-// associative and commutative, so the result does not depend on how far a
-// look-back walked.
+// k_scan  persistent blocks claim 32 KB tiles in order from an atomic
+// counter, so a block only ever waits for tiles that running blocks hold.
+// Tiles of an aligned input are staged in shared memory by bulk copies (a
+// ring of kScanStages per block), so a block has its next tiles in flight
+// while it works on one.  Per tile the block reduces the staged tile and
+// publishes its aggregate; warp 0 then looks back over the preceding tiles,
+// 32 at a time: tiles that already know their inclusive prefix end the walk,
+// the others contribute their aggregates (decoupled look-back).  The tile
+// publishes its inclusive prefix, and the block scans it a second time out of
+// shared memory, now with its prefix, and stores the outputs.  A block
+// reduces tile i + 1 before it looks back for tile i, so aggregates lead
+// look-backs by one tile.  The combiners are exact, associative and
+// commutative, so the result does not depend on how far a look-back walked
+// or in which order a tile's elements were combined.
 //
 // Status words carry an epoch (bumped by the last block of every launch), so
 // no reset pass runs between launches and graph replays see fresh flags.
 // Every wait is bounded: a wait that runs out sets kErrTimeout in the error
-// word (read by pr_last_device_error) and the tile goes on with what it has.
+// word (read by pr_last_device_error) and the block goes on with what it has.
 #include <cstring>
 #include <type_traits>
 #include "kernels.cuh"
@@ -27,8 +31,8 @@
 
 namespace pr {
 
-constexpr int kScanSpin = 1 << 18;      // polls of one flag before giving up (each >= 64 ns)
-constexpr int kScanWin = 2;             // look-back step: kScanWin x 32 tiles
+constexpr int kScanSpin = 1 << 18;      // polls of a tile state before giving up (each >= 64 ns)
+constexpr unsigned long long kScanWaitNs = 250000000ull;   // longest wait on a shared-memory barrier
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -138,12 +142,17 @@ struct ScanMaxD {
 // Accumulators of at most 32 bits share one 64-bit word with the epoch and
 // the state, so one load reads a consistent (state, value) pair: a look-back
 // step costs one L2 round trip.  Wider accumulators share a 16-byte word with
-// them, read and written by 128-bit atomics (also one round trip).
+// them, read and written by 128-bit atomics (also one round trip).  A reader
+// issues load() for many tiles at once and settle()s each word only when it
+// needs it: settle polls a word that is not yet published (bounded).
 template <bool PACKED>
 struct TileStatus;
 
 template <>
 struct TileStatus<true> {
+    struct Raw {
+        unsigned long long w;
+    };
     __device__ __forceinline__ static unsigned long long* word(ScanTile* t) {
         return reinterpret_cast<unsigned long long*>(&t->flag);
     }
@@ -153,34 +162,13 @@ struct TileStatus<true> {
     __device__ __forceinline__ static void publish(ScanTile* t, unsigned long long v, unsigned epoch, unsigned state) {
         st_relaxed_u64(word(t), ((v & 0xffffffffull) << 32) | (unsigned long long)((epoch << 2) | state));
     }
-    __device__ __forceinline__ static bool valid(unsigned long long w, unsigned epoch) {
-        const unsigned f = (unsigned)w;
+    __device__ __forceinline__ static bool valid(const Raw& r, unsigned epoch) {
+        const unsigned f = (unsigned)r.w;
         return (f >> 2) == epoch && (f & 3u) != 0u;
     }
-    // W tiles at once: the first loads all go out together; only tiles not
-    // yet published are polled again (bounded)
-    template <int W>
-    __device__ __forceinline__ static void read(ScanTile* const (&t)[W], const bool (&use)[W], unsigned epoch, int* err,
-                                                unsigned (&st)[W], unsigned long long (&v)[W], int spin = kScanSpin) {
-        unsigned long long w[W];
-#pragma unroll
-        for (int m = 0; m < W; m++) w[m] = use[m] ? ld_relaxed_u64(word(t[m])) : 0ull;
-#pragma unroll
-        for (int m = 0; m < W; m++) {
-            st[m] = 2u;
-            v[m] = 0ull;
-            if (!use[m]) continue;
-            int it = 0;
-            while (!valid(w[m], epoch) && it < spin) {
-                if (it >= 16) __nanosleep(64);
-                w[m] = ld_relaxed_u64(word(t[m]));
-                it++;
-            }
-            if (!valid(w[m], epoch)) atomicOr(err, kErrTimeout);
-            else st[m] = (unsigned)w[m] & 3u;
-            v[m] = w[m] >> 32;
-        }
-    }
+    __device__ __forceinline__ static Raw load(ScanTile* t) { return Raw{ld_relaxed_u64(word(t))}; }
+    __device__ __forceinline__ static unsigned state(const Raw& r) { return (unsigned)r.w & 3u; }
+    __device__ __forceinline__ static unsigned long long value(const Raw& r) { return r.w >> 32; }
 };
 
 // 64-bit accumulators: flag and value in one 16-byte word, written and read
@@ -203,42 +191,40 @@ __device__ __forceinline__ void read128(ScanTile* t, unsigned long long& lo, uns
 
 template <>
 struct TileStatus<false> {
+    struct Raw {
+        unsigned long long lo, hi;
+    };
     // low word: the flag ((epoch << 2) | state, as in the other layout); high word: the value
     __device__ __forceinline__ static void publish(ScanTile* t, unsigned long long v, unsigned epoch, unsigned state) {
         exch128(t, (unsigned long long)((epoch << 2) | state), v);
     }
-    __device__ __forceinline__ static bool valid(unsigned long long lo, unsigned epoch) {
-        const unsigned f = (unsigned)lo;
+    __device__ __forceinline__ static bool valid(const Raw& r, unsigned epoch) {
+        const unsigned f = (unsigned)r.lo;
         return (f >> 2) == epoch && (f & 3u) != 0u;
     }
-    template <int W>
-    __device__ __forceinline__ static void read(ScanTile* const (&t)[W], const bool (&use)[W], unsigned epoch, int* err,
-                                                unsigned (&st)[W], unsigned long long (&v)[W], int spin = kScanSpin) {
-        unsigned long long lo[W], hi[W];
-#pragma unroll
-        for (int m = 0; m < W; m++) {
-            lo[m] = 0ull;
-            hi[m] = 0ull;
-            if (use[m]) read128(t[m], lo[m], hi[m]);
-        }
-#pragma unroll
-        for (int m = 0; m < W; m++) {
-            st[m] = 2u;
-            v[m] = 0ull;
-            if (!use[m]) continue;
-            int it = 0;
-            while (!valid(lo[m], epoch) && it < spin) {
-                if (it >= 16) __nanosleep(64);
-                read128(t[m], lo[m], hi[m]);
-                it++;
-            }
-            if (!valid(lo[m], epoch)) atomicOr(err, kErrTimeout);
-            else st[m] = (unsigned)lo[m] & 3u;
-            v[m] = hi[m];
-        }
+    __device__ __forceinline__ static Raw load(ScanTile* t) {
+        Raw r;
+        read128(t, r.lo, r.hi);
+        return r;
     }
+    __device__ __forceinline__ static unsigned state(const Raw& r) { return (unsigned)r.lo & 3u; }
+    __device__ __forceinline__ static unsigned long long value(const Raw& r) { return r.hi; }
 };
 
+// Poll tile t's word until it is published in this epoch, at most `spin`
+// times; false (and kErrTimeout in the error word) if it never was.
+template <class Status>
+__device__ __forceinline__ bool settle(ScanTile* t, typename Status::Raw& r, unsigned epoch, int* err, int spin) {
+    for (int it = 0; !Status::valid(r, epoch); it++) {
+        if (it >= spin) {
+            atomicOr(err, kErrTimeout);
+            return false;
+        }
+        if (it >= 16) __nanosleep(64);
+        r = Status::load(t);
+    }
+    return true;
+}
 
 template <class Op>
 __device__ __forceinline__ typename Op::A warp_all(typename Op::A v) {
@@ -247,135 +233,405 @@ __device__ __forceinline__ typename Op::A warp_all(typename Op::A v) {
     return v;
 }
 
-// VEC: x and y aligned so that each thread's 64 input bytes and its outputs
-// move as whole 16-byte words.
-template <class Op, bool VEC>
-__global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs a) {
+// ---- bulk copies into shared memory ---------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the completion of the phase with parity `par` of a
+// shared-memory barrier: false after `limit_ns` (setting *abort_flag and
+// kErrTimeout in the error word) or as soon as *abort_flag is set.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, unsigned par, unsigned long long limit_ns,
+                                         volatile int* abort_flag, int* err) {
+    if (mbar_try_wait(bar, par)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, par)) {
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > limit_ns) {
+            *abort_flag = 1;
+            atomicOr(err, kErrTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+// global -> shared, completion counted in bytes on the barrier; both
+// addresses 16-byte aligned, size a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, unsigned bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// The look-back of tile t > 0 (one warp): the words of the W x 32 nearest
+// predecessors not yet seen are loaded at once, lane k reading tiles
+// base - k - 32 m; windows m are settled and taken nearest first, and the
+// walk ends at the first window holding an inclusive prefix, without waiting
+// for the farther ones.  Returns the combination of everything before tile t.
+template <class Op, class Status, int W>
+__device__ __forceinline__ typename Op::A look_back(const ScanArgs& a, int64_t t, unsigned epoch, int lane, int spin,
+                                                    bool& timed_out) {
+    using A = typename Op::A;
+    A pre = Op::ident();
+    for (int64_t base = t - 1;; base -= 32 * W) {
+        typename Status::Raw raw[W];
+#pragma unroll
+        for (int m = 0; m < W; m++) {
+            const int64_t j = base - lane - 32 * m;
+            if (j >= 0) raw[m] = Status::load(a.tiles + j);
+        }
+#pragma unroll
+        for (int m = 0; m < W; m++) {
+            const int64_t j = base - lane - 32 * m;
+            unsigned st = 2u;                      // before tile 0: the identity, inclusive
+            A v = Op::ident();
+            if (j >= 0) {
+                if (settle<Status>(a.tiles + j, raw[m], epoch, a.err, spin)) {
+                    st = Status::state(raw[m]);
+                    v = Op::unpack(Status::value(raw[m]));
+                } else {
+                    timed_out = true;
+                }
+            }
+            const unsigned incl = __ballot_sync(0xffffffffu, st == 2u);
+            const int stop = incl ? __ffs(incl) - 1 : 31;
+            pre = Op::comb(pre, warp_all<Op>(lane <= stop ? v : Op::ident()));
+            if (incl) return pre;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bar_sync_named(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+// named barrier that also ORs a predicate over its threads (the same result in all)
+__device__ __forceinline__ bool bar_any_named(int id, int threads, bool v) {
+    unsigned r;
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, %2, %3, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r) : "r"((unsigned)v), "r"(id), "r"(threads) : "memory");
+    return r != 0u;
+}
+
+// Warp roles and ring depth of one scan block.
+template <int S_, int NL_, int NR_, int NC_, int W_, int TB_ = kScanTileBytes, int B_ = 1, int G_ = 4>
+struct ScanShape {
+    static constexpr int G = G_;     // chunks a scan warp scans together
+    static constexpr int TB = TB_;   // tile bytes (input)
+    static constexpr int B = B_;     // most tiles claimed by one atomic
+    static constexpr int S = S_;     // shared-memory stages of TB bytes
+    static constexpr int NL = NL_;   // look-back warps (tile j: warp j mod NL)
+    static constexpr int NR = NR_;   // reduction warps
+    static constexpr int NC = NC_;   // scan-and-store warps
+    static constexpr int W = W_;     // look-back step: W x 32 tiles
+    static constexpr int kThreads = 32 * (1 + NL + NR + NC);
+};
+
+// VEC: x and y 16-byte aligned, so whole tiles are staged by bulk copies and
+// outputs leave as 16-byte words; other tiles (the ragged last one, or every
+// tile of an unaligned input) are read from x directly.
+//
+// A tile is 64 chunks of 512 bytes; lane l holds the E elements of bytes
+// [16 l, 16 l + 16) of a chunk, so shared-memory reads are conflict-free and
+// every warp store covers 512 contiguous input bytes.  Warp roles, each
+// walking the block's tiles j = 0, 1, ... through stage j mod S:
+//   warp 0, lane 0   claims a tile for a free stage and starts its copy
+//                    (full[s]: the bytes have landed);
+//   NR reduce warps  combine the tile's chunks into one total per scan warp's
+//                    slice and publish the tile aggregate (red[s]);
+//   NL look-back     look back over the preceding tiles and publish the
+//   warps            tile's inclusive prefix (pre[s]);
+//   NC scan warps    scan their slice with the prefix, store it, and release
+//                    the stage (empty[s]).
+// A claimed tile's aggregate therefore depends only on its own copy, never
+// on a look-back, so no look-back waits on another one, and the copies of
+// the next S - 1 tiles stay in flight while a tile is looked back and stored.
+template <class Op, bool VEC, class Sh>
+__global__ void __launch_bounds__(Sh::kThreads, 1) k_scan(ScanArgs a) {
     using In = typename Op::In;
     using A = typename Op::A;
     using Out = typename Op::Out;
-    constexpr int IT = kScanBytes / (int)sizeof(In);          // elements per thread
-    constexpr int64_t TILE = (int64_t)kScanThreads * IT;
-    constexpr int NW = kScanThreads / 32;
+    constexpr int S = Sh::S, NL = Sh::NL, NR = Sh::NR, NC = Sh::NC, TB = Sh::TB;
+    constexpr int E = 16 / (int)sizeof(In);                 // elements per lane and chunk
+    constexpr int CH = TB / 512;                 // chunks per tile
+    constexpr int CC = CH / NC;                              // chunks per scan slice
+    constexpr int SR = NC / NR;                              // scan slices per reduce warp
+    constexpr int CE = 32 * E;                               // elements per chunk
+    constexpr int64_t TILE = TB / (int)sizeof(In);
+    constexpr int OB = E * (int)sizeof(Out);                 // output bytes per lane and chunk
+    constexpr int G = CC < Sh::G ? CC : Sh::G;               // chunks scanned together
+    static_assert(OB == 16 || OB == 32, "outputs leave as one or two 16-byte words");
+    static_assert(CH % NC == 0 && NC % NR == 0 && NL <= S && CC % G == 0 && TB % 64 == 0, "slices split evenly");
+
+    extern __shared__ __align__(128) unsigned char s_buf[];
+    __shared__ __align__(8) unsigned long long s_bar[4 * S];  // full, red, pre, empty
+    __shared__ int64_t s_tile[S];
+    __shared__ A s_part[S][NC];
+    __shared__ A s_agg[S];
+    __shared__ A s_prefix[S];
+    __shared__ int64_t s_stop;
+    __shared__ int64_t s_last[S];                             // last tile copied into each stage
+    __shared__ int s_abort;
+    __shared__ unsigned s_epoch;
+
     const In* x = static_cast<const In*>(a.x);
     Out* y = static_cast<Out*>(a.y);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     using Status = TileStatus<(sizeof(A) <= 4)>;
-
-    __shared__ int64_t s_tile;
-    __shared__ unsigned s_epoch;
-    __shared__ A s_warp[NW];
-    __shared__ A s_prefix;
-    if (threadIdx.x == 0) s_epoch = ld_acquire_u32(a.ctr + 2) & 0x3fffffffu;
-
-    for (;;) {
-        __syncthreads();   // shared values of the previous tile are consumed
-        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(a.ctr, 1u);
-        __syncthreads();
-        const int64_t t = s_tile;
-        const unsigned epoch = s_epoch;
-        if (t >= a.ntiles) break;
-        const int64_t e0 = t * TILE + (int64_t)threadIdx.x * IT;   // this thread's first element
-        const bool full = e0 + IT <= a.n;
-
-        // 1. load and scan this thread's elements
-        A r[IT];
-        if (VEC && full) {
-            uint32_t w[kScanBytes / 4];
+    const uint32_t bars = smem_u32(s_bar), buf0 = smem_u32(s_buf);
+    auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
+    auto red = [&](int s) { return bars + 8u * (uint32_t)(S + s); };
+    auto pre = [&](int s) { return bars + 8u * (uint32_t)(2 * S + s); };
+    auto empty = [&](int s) { return bars + 8u * (uint32_t)(3 * S + s); };
+    volatile int* abort_flag = &s_abort;
+    // a wait that runs out, or sees that another warp gave up, returns false
+    // and the block winds down (every role leaves its loop)
+    auto wait = [&](uint32_t bar, unsigned par) { return bar_wait(bar, par, kScanWaitNs, abort_flag, a.err); };
+    auto staged = [&](int64_t t) { return VEC && (t + 1) * TILE <= a.n; };
+    // chunk c of tile t for this lane, from stage s or from x
+    auto load_chunk = [&](int s, int64_t t, bool st, int c, A (&v)[E]) {
+        if (st) {
+            const uint4 w = *reinterpret_cast<const uint4*>(s_buf + s * TB + c * 512 + lane * 16);
+            In e[E];
+            memcpy(e, &w, 16);
 #pragma unroll
-            for (int q = 0; q < kScanBytes / 32; q++) {
-                const Words<32> v = ldv<32>(x + e0 + q * (32 / (int)sizeof(In)));
-                memcpy(w + q * 8, v.w, 32);
-            }
-            In e[IT];
-            memcpy(e, w, kScanBytes);
-#pragma unroll
-            for (int k = 0; k < IT; k++) r[k] = Op::conv(e[k]);
+            for (int j = 0; j < E; j++) v[j] = Op::conv(e[j]);
         } else {
+            const int64_t i0 = t * TILE + (int64_t)c * CE + lane * E;
 #pragma unroll
-            for (int k = 0; k < IT; k++) r[k] = e0 + k < a.n ? Op::conv(x[e0 + k]) : Op::ident();
+            for (int j = 0; j < E; j++) v[j] = i0 + j < a.n ? Op::conv(x[i0 + j]) : Op::ident();
         }
-#pragma unroll
-        for (int k = 1; k < IT; k++) r[k] = Op::comb(r[k - 1], r[k]);
+    };
 
-        // 2. block scan of the thread totals
-        A inc = r[IT - 1];
+    if (threadIdx.x == 0) {
+        s_epoch = ld_acquire_u32(a.ctr + 2) & 0x3fffffffu;
+        s_stop = INT64_MAX;
+        s_abort = 0;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const A o = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc = Op::comb(o, inc);
+        for (int s = 0; s < S; s++) {
+            s_last[s] = -1;
+            mbar_init(full(s), 1u);
+            mbar_init(red(s), 1u);
+            mbar_init(pre(s), 1u);
+            mbar_init(empty(s), (unsigned)NC);
         }
-        if (lane == 31) s_warp[warp] = inc;
-        __syncthreads();
-        A wpre = Op::ident(), agg = Op::ident();
-#pragma unroll
-        for (int w = 0; w < NW; w++) {
-            if (w < warp) wpre = Op::comb(wpre, s_warp[w]);
-            agg = Op::comb(agg, s_warp[w]);
-        }
-        A texcl = __shfl_up_sync(0xffffffffu, inc, 1);
-        texcl = lane == 0 ? wpre : Op::comb(wpre, texcl);   // everything before this thread in the tile
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const unsigned epoch = s_epoch;
 
-        // 3. publish the aggregate, look back, publish the inclusive prefix
-        if (warp == 0) {
-            A pre = Op::ident();
-            if (t == 0) {
-                if (lane == 0) Status::publish(a.tiles, Op::pack(agg), epoch, 2u);
-            } else {
-                if (lane == 0) Status::publish(a.tiles + t, Op::pack(agg), epoch, 1u);
-                // windows of kScanWin x 32 predecessors: lane k reads tiles
-                // base - k - 32 m; sub-windows are taken nearest first
-                for (int64_t base = t - 1;; base -= 32 * kScanWin) {
-                    ScanTile* tp[kScanWin];
-                    bool use[kScanWin];
+    if (warp == 0) {
+        // ---- producer: claim, copy ----
+        if (lane == 0) {
+            // stage j mod S is free once the scan warps released tile j - S
+            auto is_free = [&](int64_t j) {
+                return j < S || mbar_test_wait(empty((int)(j % S)), (unsigned)((j / S - 1) & 1));
+            };
+            bool done = false;
+            for (int64_t j = 0; !done;) {
+                if (*abort_flag || (j >= S && !wait(empty((int)(j % S)), (unsigned)((j / S - 1) & 1)))) break;
+                // one claim covers every stage that is free now (at most B)
+                int k = 1;
+                while (k < Sh::B && is_free(j + k)) k++;
+                const int64_t t0 = (int64_t)atomicAdd(a.ctr, (unsigned)k);
+                for (int i = 0; i < k && !done; i++, j++) {
+                    const int s = (int)(j % S);
+                    const int64_t t = t0 + i;
+                    s_tile[s] = t;
+                    if (t < a.ntiles && staged(t)) {
+                        s_last[s] = j;
+                        mbar_expect_tx(full(s), (unsigned)TB);
+                        const char* src = reinterpret_cast<const char*>(x) + t * TB;
 #pragma unroll
-                    for (int m = 0; m < kScanWin; m++) {
-                        const int64_t j = base - lane - 32 * m;
-                        use[m] = j >= 0;
-                        tp[m] = a.tiles + (j >= 0 ? j : 0);
+                        for (int c = 0; c < 4; c++)
+                            bulk_g2s(buf0 + (uint32_t)(s * TB + c * (TB / 4)), src + c * (TB / 4), (unsigned)(TB / 4),
+                                     full(s));
+                    } else {
+                        mbar_arrive(full(s));
                     }
-                    unsigned st[kScanWin];
-                    unsigned long long vb[kScanWin];
-                    Status::template read<kScanWin>(tp, use, epoch, a.err, st, vb);
-                    bool found = false;
-#pragma unroll
-                    for (int m = 0; m < kScanWin; m++) {
-                        if (found) break;
-                        const A v = use[m] ? Op::unpack(vb[m]) : Op::ident();
-                        const unsigned incl = __ballot_sync(0xffffffffu, st[m] == 2u);
-                        const int stop = incl ? __ffs(incl) - 1 : 31;
-                        pre = Op::comb(pre, warp_all<Op>(lane <= stop ? v : Op::ident()));
-                        found = incl != 0u;
-                    }
-                    if (found) break;
+                    done = t >= a.ntiles;
                 }
-                if (lane == 0) Status::publish(a.tiles + t, Op::pack(Op::comb(pre, agg)), epoch, 2u);
             }
-            if (lane == 0) s_prefix = pre;
         }
-        __syncthreads();
-        const A base = Op::comb(s_prefix, texcl);
+    } else if (warp <= NL) {
+        // ---- look-back: tiles j = l, l + NL, ... ----
+        for (int64_t j = warp - 1;; j += NL) {
+            const int s = (int)(j % S);
+            if (!__all_sync(0xffffffffu, wait(red(s), (unsigned)((j / S) & 1)))) break;
+            const int64_t t = s_tile[s];
+            if (j >= s_stop) break;                        // past the last tile, woken by the reducers
+            if (t >= a.ntiles) {
+                if (lane == 0) mbar_arrive(pre(s));
+                break;
+            }
+            A p = Op::ident();
+            if (t != 0) {
+                bool late = false;
+                p = look_back<Op, Status, Sh::W>(a, t, epoch, lane, *abort_flag ? 1 : kScanSpin, late);
+                if (__any_sync(0xffffffffu, late)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                if (lane == 0) Status::publish(a.tiles + t, Op::pack(Op::comb(p, s_agg[s])), epoch, 2u);
+            }
+            if (lane == 0) {
+                s_prefix[s] = p;
+                mbar_arrive(pre(s));
+            }
+        }
+    } else if (warp <= NL + NR) {
+        // ---- reduce: slice totals and the tile aggregate ----
+        const int r = warp - 1 - NL;
+        for (int64_t j = 0;; j++) {
+            const int s = (int)(j % S);
+            // the reduce warps leave together (they share a named barrier)
+            const bool ok = wait(full(s), (unsigned)((j / S) & 1));
+            if (bar_any_named(1, 32 * NR, !ok || *abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            const int64_t t = s_tile[s];
+            if (t >= a.ntiles) {
+                if (r == 0 && lane == 0) {
+                    s_stop = j + 1;                         // look-back warps waiting on later tiles stop
+                    for (int i = 0; i < NL; i++) mbar_arrive(red((int)((j + i) % S)));
+                }
+                break;
+            }
+            const bool st = staged(t);
+#pragma unroll
+            for (int q = 0; q < SR; q++) {
+                A tot = Op::ident();
+#pragma unroll 4
+                for (int c = 0; c < CC; c++) {
+                    A v[E];
+                    load_chunk(s, t, st, (r * SR + q) * CC + c, v);
+#pragma unroll
+                    for (int i = 0; i < E; i++) tot = Op::comb(tot, v[i]);
+                }
+                tot = warp_all<Op>(tot);
+                if (lane == 0) s_part[s][r * SR + q] = tot;
+            }
+            bar_sync_named(1, 32 * NR);
+            if (r == 0 && lane == 0) {
+                A agg = Op::ident();
+#pragma unroll
+                for (int c = 0; c < NC; c++) agg = Op::comb(agg, s_part[s][c]);
+                s_agg[s] = agg;
+                Status::publish(a.tiles + t, Op::pack(agg), epoch, t == 0 ? 2u : 1u);
+                mbar_arrive(red(s));
+            }
+        }
+    } else {
+        // ---- scan and store one slice ----
+        const int c0 = warp - 1 - NL - NR;
+        for (int64_t j = 0;; j++) {
+            const int s = (int)(j % S);
+            const unsigned par = (unsigned)((j / S) & 1);
+            if (!__all_sync(0xffffffffu, wait(pre(s), par))) break;
+            const int64_t t = s_tile[s];
+            if (t >= a.ntiles) break;
+            const bool st = staged(t);
+            if (st && !__all_sync(0xffffffffu, wait(full(s), par))) break;   // the copied bytes, seen by this warp
+            A carry = s_prefix[s];
+#pragma unroll
+            for (int c = 0; c < NC; c++)
+                if (c < c0) carry = Op::comb(carry, s_part[s][c]);
+            // G chunks at a time: their warp scans are independent, so the
+            // shuffle chains overlap; the carry then runs through them in order
+            for (int c = c0 * CC; c < (c0 + 1) * CC; c += G) {
+                A v[G][E], inc[G], ex[G], tot[G];
+#pragma unroll
+                for (int g = 0; g < G; g++) {
+                    load_chunk(s, t, st, c + g, v[g]);
+#pragma unroll
+                    for (int i = 1; i < E; i++) v[g][i] = Op::comb(v[g][i - 1], v[g][i]);
+                    inc[g] = v[g][E - 1];
+                }
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+                    for (int g = 0; g < G; g++) {
+                        const A o = __shfl_up_sync(0xffffffffu, inc[g], d);
+                        if (lane >= d) inc[g] = Op::comb(o, inc[g]);
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < G; g++) {
+                    ex[g] = __shfl_up_sync(0xffffffffu, inc[g], 1);
+                    tot[g] = __shfl_sync(0xffffffffu, inc[g], 31);
+                }
+#pragma unroll
+                for (int g = 0; g < G; g++) {
+                    const A cb = lane == 0 ? carry : Op::comb(carry, ex[g]);
+                    carry = Op::comb(carry, tot[g]);
+                    Out o[E];
+#pragma unroll
+                    for (int i = 0; i < E; i++)
+                        o[i] = Op::out(a.exclusive ? (i == 0 ? cb : Op::comb(cb, v[g][i - 1])) : Op::comb(cb, v[g][i]));
+                    const int64_t i0 = t * TILE + (int64_t)(c + g) * CE + lane * E;
+                    if (st) {
+                        uint32_t w[OB / 4];
+                        memcpy(w, o, OB);
+                        char* dst = reinterpret_cast<char*>(y + i0);
+#pragma unroll
+                        for (int h = 0; h < OB / 16; h++)
+                            asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(dst + 16 * h), "r"(w[4 * h]),
+                                         "r"(w[4 * h + 1]), "r"(w[4 * h + 2]), "r"(w[4 * h + 3]) : "memory");
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < E; i++)
+                            if (i0 + i < a.n) y[i0 + i] = o[i];
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty(s));
+        }
+    }
 
-        // 4. outputs
-        Out o[IT];
-#pragma unroll
-        for (int k = 0; k < IT; k++) {
-            const A v = a.exclusive ? (k == 0 ? base : Op::comb(base, r[k - 1])) : Op::comb(base, r[k]);
-            o[k] = Op::out(v);
-        }
-        if (VEC && full) {
-            constexpr int OB = IT * (int)sizeof(Out);
-            uint32_t w[OB / 4];
-            memcpy(w, o, OB);
-            char* dst = reinterpret_cast<char*>(y + e0);
-#pragma unroll
-            for (int q = 0; q < OB / 16; q++)
-                asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(dst + q * 16), "r"(w[4 * q]),
-                             "r"(w[4 * q + 1]), "r"(w[4 * q + 2]), "r"(w[4 * q + 3]) : "memory");
-        } else {
-#pragma unroll
-            for (int k = 0; k < IT; k++)
-                if (e0 + k < a.n) y[e0 + k] = o[k];
+    __syncthreads();
+    // a block that gave up waits (bounded) for the copies it started, so none
+    // lands in shared memory after the block has left
+    if (threadIdx.x == 0 && s_abort) {
+        for (int s = 0; s < S; s++) {
+            if (s_last[s] < 0) continue;
+            const uint32_t bar = full(s);
+            const unsigned par = (unsigned)((s_last[s] / S) & 1);
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try_wait(bar, par) && global_ns() - t0 < kScanWaitNs) {
+            }
         }
     }
     // the last block out re-arms the tile counter and moves to the next epoch
@@ -390,17 +646,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs a) {
     }
 }
 
-// Self-check of the bounded wait: one thread waits, with `spin` polls, on a
-// tile state that nothing publishes; the wait must give up and set
-// kErrTimeout in the error word.
+// Self-check of the bounded waits: one thread waits, with `spin` polls, on a
+// tile state that nothing publishes (both layouts), and for spin
+// microseconds on a shared-memory barrier phase that nothing completes; each
+// wait must give up and set kErrTimeout in the error word.
 __global__ void k_wait_probe(ScanTile* t, int spin, int* err) {
+    __shared__ __align__(8) unsigned long long s_b;
+    __shared__ int s_give_up;
     if (threadIdx.x != 0) return;
-    ScanTile* tp[1] = {t};
-    const bool use[1] = {true};
-    unsigned st[1];
-    unsigned long long v[1];
-    TileStatus<true>::read<1>(tp, use, 1u, err, st, v, spin);
-    TileStatus<false>::read<1>(tp, use, 1u, err, st, v, spin);
+    TileStatus<true>::Raw r1 = TileStatus<true>::load(t);
+    settle<TileStatus<true>>(t, r1, 1u, err, spin);
+    TileStatus<false>::Raw r2 = TileStatus<false>::load(t);
+    settle<TileStatus<false>>(t, r2, 1u, err, spin);
+    s_give_up = 0;
+    const uint32_t bar = smem_u32(&s_b);
+    mbar_init(bar, 1u);
+    mbar_fence_init();
+    bar_wait(bar, 0u, 1000ull * (unsigned long long)spin, &s_give_up, err);
 }
 
 cudaError_t launch_wait_probe(ScanTile* t, int spin, int* err, cudaStream_t st) {
@@ -408,9 +670,12 @@ cudaError_t launch_wait_probe(ScanTile* t, int spin, int* err, cudaStream_t st) 
     return cudaGetLastError();
 }
 
+using ScanMain = ScanShape<kScanStages, kScanLookWarps, kScanRedWarps, kScanScanWarps, kScanLookWin>;
+static_assert(ScanMain::kThreads == kScanThreads, "block size of the scan");
+
 template <class Op, bool VEC>
-cudaError_t launch_scan(const ScanArgs& a, int grid, int block, cudaStream_t st) {
-    k_scan<Op, VEC><<<grid, block, 0, st>>>(a);
+cudaError_t launch_scan(const ScanArgs& a, int grid, int block, size_t smem, cudaStream_t st) {
+    k_scan<Op, VEC, ScanMain><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -418,9 +683,11 @@ cudaError_t launch_scan(const ScanArgs& a, int grid, int block, cudaStream_t st)
 template <class Op>
 static void reg_scan(uint8_t dtype, uint8_t op) {
     reg_add(KernelKey{K_SCAN, dtype, op, 0, 0, 0, 0},
-            KernelEntry{reinterpret_cast<const void*>(&k_scan<Op, false>), reinterpret_cast<void*>(&launch_scan<Op, false>)});
+            KernelEntry{reinterpret_cast<const void*>(&k_scan<Op, false, ScanMain>),
+                        reinterpret_cast<void*>(&launch_scan<Op, false>)});
     reg_add(KernelKey{K_SCAN, dtype, op, 0, 0, 0, 1},
-            KernelEntry{reinterpret_cast<const void*>(&k_scan<Op, true>), reinterpret_cast<void*>(&launch_scan<Op, true>)});
+            KernelEntry{reinterpret_cast<const void*>(&k_scan<Op, true, ScanMain>),
+                        reinterpret_cast<void*>(&launch_scan<Op, true>)});
 }
 
 template <class In, class ASum, class A>

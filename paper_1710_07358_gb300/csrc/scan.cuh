@@ -29,13 +29,17 @@ struct ScanArgs {
     int* err;
 };
 
-// Tiles of 256 x 128 input bytes (32 KB).  A block serialises claim, load,
-// look-back and stores per tile, and the look-back frontier must keep up with
-// the tiles HBM streams in, so tiles are large and several blocks share an SM
-// (measured on GB300, 2^28 uint32 prefix sums: 16 KB tiles 601 us, 32 KB tiles
-// 544 us, 64 KB tiles 661 us).
-constexpr int kScanThreads = 256;
-constexpr int kScanBytes = 128;         // input bytes per thread and tile
+// Tiles of 32 KB of input, staged in a ring of kScanStages shared-memory
+// buffers per block (224 KB: one block per SM).  Warps: one producer,
+// kScanLookWarps look-back, kScanRedWarps reduction and kScanScanWarps
+// scan-and-store warps; a look-back step reads kScanLookWin x 32 tile states.
+constexpr int kScanTileBytes = 32768;
+constexpr int kScanStages = 7;
+constexpr int kScanLookWarps = 2;
+constexpr int kScanRedWarps = 4;
+constexpr int kScanScanWarps = 8;
+constexpr int kScanLookWin = 1;
+constexpr int kScanThreads = 32 * (1 + kScanLookWarps + kScanRedWarps + kScanScanWarps);
 
 // One bounded wait on a tile state nothing publishes (zero-filled, epoch 1).
 cudaError_t launch_wait_probe(ScanTile* t, int spin, int* err, cudaStream_t st);

@@ -55,7 +55,8 @@ def run(x, dtype, op, exclusive, offset=0):
     return got_values(y, dtype, op)
 
 
-SIZES = [1, 5, 4095, 4096, 4097, 100000, (1 << 20) + 3]
+# around the 32 KB tile (8192 4-byte elements; 4096 8-byte, 16384 2-byte)
+SIZES = [1, 5, 4095, 4096, 4097, 8191, 8192, 8193, 3 * 8192, 100000, (1 << 20) + 3]
 
 
 @pytest.mark.parametrize("n", SIZES)
@@ -78,6 +79,19 @@ def test_scan_dtypes(dtype, op, offset):
     x = gen(dtype, n, 3 + offset)
     for exclusive in (False, True):
         assert_same(run(x, dtype, op, exclusive, offset), oracle.scan(x, dtype, op, exclusive), dtype)
+
+
+@pytest.mark.parametrize("dtype,op", [("i64", "sum"), ("f64", "max"), ("bf16", "max"), ("u32", "or")])
+@pytest.mark.parametrize("tiles", [1, 2, 7, 300])
+def test_scan_whole_tiles(dtype, op, tiles):
+    """n an exact number of 32 KB tiles and one element either side: every
+    tile staged, then a one-element ragged tail, then one element short."""
+    es = {"i64": 8, "f64": 8, "bf16": 2, "u32": 4}[dtype]
+    base = tiles * (32768 // es)
+    for n in (base - 1, base, base + 1):
+        x = gen(dtype, n, tiles + n)
+        for exclusive in (False, True):
+            assert_same(run(x, dtype, op, exclusive), oracle.scan(x, dtype, op, exclusive), dtype)
 
 
 def test_scan_float_nan_and_signed_zeros():
