@@ -148,6 +148,7 @@ def test_scan_rejects(L):
     assert pr.pr_scan(FAKE + 2, 4, I32, MAX, 0, FAKE, None) == INVALID
     assert pr.pr_scan(FAKE, 4, I32, SUM, 0, FAKE + 4, None) == INVALID   # int64 output alignment
     assert pr.pr_scan(None, 0, I32, SUM, 0, None, None) == OK
+    assert pr.pr_scan(FAKE, 1 << 45, U32, SUM, 0, FAKE, None) == INVALID   # 2^32 tiles of 32 KB
     assert pr.pr_check_bounded_wait(0, None) == INVALID
 
 

@@ -94,6 +94,24 @@ def test_scan_whole_tiles(dtype, op, tiles):
             assert_same(run(x, dtype, op, exclusive), oracle.scan(x, dtype, op, exclusive), dtype)
 
 
+@pytest.mark.parametrize("dtype,op", [("u32", "sum"), ("i32", "sum"), ("f32", "min")])
+def test_scan_unaligned_output(dtype, op):
+    """x aligned but y one element past a 16-byte boundary: every tile is read
+    and written element-wise, with the same result."""
+    import torch
+    n = 5 * 8192 + 77
+    x = gen(dtype, n, 9)
+    t = to_device(x, dtype)
+    od = pr.out_dtype_name(dtype, op)
+    buf = torch.zeros(n + 1, dtype=pr.torch_dtype(od), device="cuda")
+    y = buf[1:]
+    assert y.data_ptr() % 16 != 0
+    for exclusive in (False, True):
+        pr.scan(t, op, exclusive=exclusive, out=y)
+        assert_same(got_values(y, dtype, op), oracle.scan(x, dtype, op, exclusive), dtype)
+    assert buf[0].item() == 0
+
+
 def test_scan_float_nan_and_signed_zeros():
     n = 50000
     x = synth.normal_f32(n, 5)
