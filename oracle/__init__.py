@@ -6,6 +6,8 @@ The product path never imports this package and shares no code with it.
 
 The arithmetic lives in ``oracle.c`` (plain sequential loops, exact or
 extended-precision accumulation); this module only marshals numpy arrays.
+The line search built on the reduction (golden-section and Fibonacci search
+of the Beckmann objective) is plain float64 Python in ``linesearch.py``.
 
 Dtype names: f32 f16 bf16 f64 i32 u32 i64.  bf16 and f16 arrays are passed as
 their 16-bit patterns (``uint16``; an ``np.float16`` array is viewed as such).
