@@ -107,6 +107,9 @@ typedef enum {
     PR_KIND_REDUCE = 0, PR_KIND_SEGMENTED = 1, PR_KIND_BACKWARD = 2, PR_KIND_ROWS = 3, PR_KIND_AXIS = 4
 } pr_kind;
 
+/* Line-search methods (pr_line_search). */
+typedef enum { PR_SEARCH_GOLDEN = 0, PR_SEARCH_FIBONACCI = 1 } pr_search;
+
 /* Per-segment state that the product's gradient needs. */
 typedef struct {
     double p_nz;          /* product of the non-zero elements (as double) */
@@ -220,6 +223,50 @@ pr_status pr_scan(const void* x, int64_t n, pr_dtype dtype, pr_op op, int32_t ex
  * stream's device error word (read it with pr_last_device_error); the
  * context stays usable. */
 pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Line search with the reduction as its inner step                        */
+/* ---------------------------------------------------------------------- */
+
+/* The Beckmann objective of BPR link costs along a direction, the function
+ * the golden-ratio step of Section 5's traffic assignment minimises (each
+ * evaluation one reduction over all links):
+ *   phi(alpha) = sum_i t0[i] (v_i + beta cap[i] / (power + 1) (v_i / cap[i])^(power + 1)),
+ *   v_i = x[i] + alpha d[i].
+ * x (flows), d (direction), t0 (free-flow times), cap (capacities > 0): n
+ * float32 each, device memory, 4-byte aligned (16-byte aligned: vector
+ * loads).  beta >= 0, power in [1, 16].  Terms are evaluated in float32 and
+ * summed per point with TwoSum, then combined in float64 in a fixed order:
+ * deterministic, within about (power + 4) 2^-24 sum |term| of the exact sum.
+ *
+ * pr_beckmann: out[k] = phi(alphas[k]) for k < m, m in [1, 16], in one pass
+ * over the links (alphas and out: device, 8-byte aligned; alphas rounded to
+ * float32 for the evaluation).
+ *
+ * pr_line_search: minimises phi on [lo, hi] (finite, lo < hi).
+ *   PR_SEARCH_GOLDEN: golden-section search (points b - r (b - a) and
+ *     a + r (b - a), r = (sqrt 5 - 1) / 2) with `count` iterations in
+ *     [0, 200] after the first two evaluations: the bracket ends
+ *     (hi - lo) r^count wide.
+ *   PR_SEARCH_FIBONACCI: Fibonacci search with `count` evaluations in
+ *     [3, 78]: points a_j + F_{N-j-1} u and a_j + F_{N-j} u, u = (hi - lo) /
+ *     F_N (F_0 = F_1 = 1), the last one a tenth of u from the retained point;
+ *     the bracket ends u or 1.1 u wide.
+ * Each iteration keeps [a, x2] when phi(x1) < phi(x2), else [x1, b] (ties),
+ * and evaluates one new point; the points are placed in float64 with the
+ * expressions above evaluated left to right.  `depth` in [1, 3]: one pass
+ * over the links evaluates every point the next `depth` iterations could
+ * need (2^(depth+1) - 2 of them), so a search costs about count / depth
+ * passes; the sequence of points is that of the one-by-one search.  The
+ * state lives on the device (a per-stream buffer made on first use, outside
+ * graph capture): nothing is synchronised, and result (device, 4 doubles:
+ * final a, b, the better of the last two points, its phi) is written by the
+ * last kernel of the call. */
+pr_status pr_beckmann(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
+                      int32_t power, const double* alphas, int32_t m, double* out, pr_stream_t stream);
+pr_status pr_line_search(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
+                         int32_t power, double lo, double hi, pr_search method, int32_t count, int32_t depth,
+                         double* result, pr_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
 /* Differentiation of a row reduction (F32 and F64)                         */

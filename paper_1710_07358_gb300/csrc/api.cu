@@ -1,6 +1,7 @@
 // C ABI of libpr.so (declared in include/pr.h): argument validation,
 // per-(device, stream) workspaces, launch-configuration lookup and tuning,
 // and the host-memory pipeline.  All arithmetic runs in the kernels.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,7 @@
 #include "kernels.cuh"
 #include "registry.h"
 #include "scan.cuh"
+#include "search.cuh"
 
 namespace pr {
 
@@ -111,6 +113,7 @@ struct WsRec {
     size_t axis_bytes = 0;
     void* scan = nullptr;    // scan tile states + counters, grown on demand
     size_t scan_tiles = 0;
+    void* search = nullptr;  // line-search state + evaluation partials, made on first use
 };
 static std::map<std::pair<int, cudaStream_t>, WsRec> g_ws;
 
@@ -556,6 +559,40 @@ static pr_status scan_state(cudaStream_t st, int64_t tiles, ScanTile** recs, uns
     return PR_OK;
 }
 
+// Line-search state for (device, stream): the LsState, gmax x kLsMaxPts
+// evaluation partials and one ticket, made zero-filled on first use (outside
+// graph capture).
+static pr_status search_state(cudaStream_t st, LsState** state, double** partials, unsigned** ticket) {
+    Workspace ws;
+    pr_status s = get_ws(st, &ws);
+    if (s != PR_OK) return s;
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    WsRec& w = g_ws[std::make_pair(dev, st)];
+    const size_t head = (sizeof(LsState) + 255) / 256 * 256;
+    const size_t parts = (size_t)ws.gmax * kLsMaxPts * sizeof(double);
+    if (!w.search) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        PR_CUDA(cudaStreamIsCapturing(st, &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(PR_ERR_INVALID, "line-search state: run a search on this stream once before graph capture");
+        PR_CUDA(cudaStreamSynchronize(st));
+        const size_t bytes = head + parts + 256;
+        if (cudaMalloc(&w.search, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            w.search = nullptr;
+            return fail(PR_ERR_NOMEM, "line-search state: allocation of %zu bytes failed", bytes);
+        }
+        PR_CUDA(cudaMemset(w.search, 0, bytes));
+    }
+    char* b = static_cast<char*>(w.search);
+    *state = reinterpret_cast<LsState*>(b);
+    *partials = reinterpret_cast<double*>(b + head);
+    *ticket = reinterpret_cast<unsigned*>(b + head + parts);
+    return PR_OK;
+}
+
 static pr_status run_axis_backward(int op, int dtype, const void* x, int64_t outer, int64_t n, int64_t inner,
                                    const void* g, const int64_t* argidx, const pr_prod_aux* aux, void* gi,
                                    cudaStream_t st) {
@@ -857,6 +894,101 @@ pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream) {
     cudaError_t err = launch_wait_probe(rec, polls, ws.err, st);
     cudaFreeAsync(rec, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "wait probe launch: %s", cudaGetErrorString(err));
+    return PR_OK;
+}
+
+// ------------------------------------------------------------------------
+// Line search on the reduction
+// ------------------------------------------------------------------------
+
+static pr_status check_links(const float* x, const float* d, const float* t0, const float* cap, int64_t n,
+                             float beta, int32_t power) {
+    if (n < 0) return fail(PR_ERR_INVALID, "n must be >= 0");
+    if (n > 0 && (!x || !d || !t0 || !cap)) return fail(PR_ERR_INVALID, "a link array is NULL");
+    const float* arr[4] = {x, d, t0, cap};
+    for (const float* p : arr)
+        if (reinterpret_cast<uintptr_t>(p) % 4) return fail(PR_ERR_INVALID, "link arrays must be 4-byte aligned");
+    if (!(beta >= 0.f) || !std::isfinite(beta)) return fail(PR_ERR_INVALID, "beta must be finite and >= 0");
+    if (power < 1 || power > 16) return fail(PR_ERR_INVALID, "power must be in [1, 16]");
+    return PR_OK;
+}
+
+// One evaluation pass: m points of pts, sums into out (all device memory).
+static pr_status run_phi(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
+                         int32_t power, const double* pts, int m, double* out, double* partials, unsigned* ticket,
+                         cudaStream_t st) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(d) |
+                       reinterpret_cast<uintptr_t>(t0) | reinterpret_cast<uintptr_t>(cap)) % 16) == 0;
+    DevInfo di;
+    pr_status s = device_info(&di, nullptr);
+    if (s != PR_OK) return s;
+    int occ = 0;
+    if ((s = occupancy(phi_kernel(vec, power), kPhiThreads, &occ)) != PR_OK) return s;
+    if (occ < 1) return fail(PR_ERR_UNSUPPORTED, "evaluation kernel cannot run");
+    Workspace ws;
+    if ((s = get_ws(st, &ws)) != PR_OK) return s;
+    int64_t grid = (int64_t)di.sms * occ;
+    const int64_t need = (n + 4LL * kPhiThreads - 1) / (4LL * kPhiThreads);
+    if (grid > need) grid = need > 0 ? need : 1;
+    if (grid > ws.gmax) grid = ws.gmax;
+    PhiArgs a{x, d, t0, cap, n, beta, power, pts, m, out, partials, ticket};
+    cudaError_t err = launch_phi(a, (int)grid, vec, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "evaluation launch: %s", cudaGetErrorString(err));
+    return PR_OK;
+}
+
+pr_status pr_beckmann(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
+                      int32_t power, const double* alphas, int32_t m, double* out, pr_stream_t stream) {
+    g_msg.clear();
+    pr_status s = check_links(x, d, t0, cap, n, beta, power);
+    if (s != PR_OK) return s;
+    if (m < 1 || m > kLsMaxPts) return fail(PR_ERR_INVALID, "m must be in [1, %d]", kLsMaxPts);
+    if (!alphas || !out) return fail(PR_ERR_INVALID, "alphas / out is NULL");
+    if (reinterpret_cast<uintptr_t>(alphas) % 8 || reinterpret_cast<uintptr_t>(out) % 8)
+        return fail(PR_ERR_INVALID, "alphas / out must be 8-byte aligned");
+    ensure_registered();
+    cudaStream_t st = (cudaStream_t)stream;
+    LsState* ls = nullptr;
+    double* parts = nullptr;
+    unsigned* ticket = nullptr;
+    if ((s = search_state(st, &ls, &parts, &ticket)) != PR_OK) return s;
+    return run_phi(x, d, t0, cap, n, beta, power, alphas, m, out, parts, ticket, st);
+}
+
+pr_status pr_line_search(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
+                         int32_t power, double lo, double hi, pr_search method, int32_t count, int32_t depth,
+                         double* result, pr_stream_t stream) {
+    g_msg.clear();
+    pr_status s = check_links(x, d, t0, cap, n, beta, power);
+    if (s != PR_OK) return s;
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi)) return fail(PR_ERR_INVALID, "need finite lo < hi");
+    if (method != PR_SEARCH_GOLDEN && method != PR_SEARCH_FIBONACCI) return fail(PR_ERR_INVALID, "unknown method");
+    if (method == PR_SEARCH_GOLDEN && (count < 0 || count > 200))
+        return fail(PR_ERR_INVALID, "golden-section iterations must be in [0, 200]");
+    if (method == PR_SEARCH_FIBONACCI && (count < 3 || count > 78))
+        return fail(PR_ERR_INVALID, "Fibonacci evaluations must be in [3, 78]");
+    if (depth < 1 || depth > kLsMaxDepth) return fail(PR_ERR_INVALID, "depth must be in [1, %d]", kLsMaxDepth);
+    if (!result || reinterpret_cast<uintptr_t>(result) % 8) return fail(PR_ERR_INVALID, "result must be 8-byte aligned");
+    ensure_registered();
+    cudaStream_t st = (cudaStream_t)stream;
+    LsState* ls = nullptr;
+    double* parts = nullptr;
+    unsigned* ticket = nullptr;
+    if ((s = search_state(st, &ls, &parts, &ticket)) != PR_OK) return s;
+    const int total = method == PR_SEARCH_GOLDEN ? count : count - 2;
+    cudaError_t err = launch_ls_init(ls, lo, hi, (int)method, count, total, depth, st);
+    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "search init launch: %s", cudaGetErrorString(err));
+    // passes: the first evaluates x1, x2 and the next min(depth, total)
+    // iterations' tree, each later one the next min(depth, left) iterations'
+    int iter = 0;
+    for (bool first = true; first || iter < total; first = false) {
+        const int lv = total - iter < depth ? total - iter : depth;
+        const int m = (first ? 2 : 0) + (2 << lv) - 2;
+        if ((s = run_phi(x, d, t0, cap, n, beta, power, ls->pts, m, ls->vals, parts, ticket, st)) != PR_OK) return s;
+        err = launch_ls_update(ls, result, st);
+        if (err != cudaSuccess) return fail(PR_ERR_CUDA, "search update launch: %s", cudaGetErrorString(err));
+        iter += lv;
+    }
     return PR_OK;
 }
 

@@ -1,0 +1,339 @@
+// Line search whose inner step is the reduction: golden-section and Fibonacci
+// search (Section 1 names them among the reduction's consumers; Section 5 uses
+// the golden-ratio method in the traffic assignment step) of the Beckmann
+// objective of BPR link costs along a direction,
+//
+//   phi(alpha) = sum_i t0_i (v_i + beta c_i / (p + 1) (v_i / c_i)^(p + 1)),
+//   v_i = x_i + alpha d_i.
+//
+// k_phi      one pass over the four float32 link arrays evaluates phi at up
+//            to kLsMaxPts points: each term in float32, accumulated per point
+//            with TwoSum (error-free) into (sum, compensation) pairs, combined
+//            per block in float64 and by the last block in block order (the
+//            persistent reduction of Section 3 with a fixed combine order).
+// k_ls_init  places the first two points and the speculative tree.
+// k_ls_update walks depth D decisions with the values of the pass, then places
+//            the next pass's tree: the 2^(D+1) - 2 points the next D
+//            iterations could need, so that D iterations cost one pass over
+//            the links instead of D, and the sequence of points is exactly
+//            the sequential search's.
+// Both small kernels run on one thread, with float64 operations written
+// out (no contraction into FMA), so that the points match a float64
+// implementation that evaluates the same expressions in the same order.
+#include <cstdint>
+#include "kernels.cuh"
+#include "search.cuh"
+
+namespace pr {
+
+// ---- evaluation pass -------------------------------------------------------
+
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
+    const float t = s + v;
+    const float bp = t - s;
+    const float ap = t - bp;
+    c = c + ((s - ap) + (v - bp));
+    s = t;
+}
+
+// (v / c)^(p + 1) by repeated squaring for the usual powers
+template <int PW>
+__device__ __forceinline__ float pow_p1(float q, int power) {
+    if constexpr (PW == 1) return q * q;
+    else if constexpr (PW == 2) return (q * q) * q;
+    else if constexpr (PW == 3) { const float q2 = q * q; return q2 * q2; }
+    else if constexpr (PW == 4) { const float q2 = q * q; return (q2 * q2) * q; }
+    else {
+        float r = q;
+        for (int k = 0; k < power; k++) r *= q;
+        return r;
+    }
+}
+
+template <int PW>
+__device__ __forceinline__ void phi_link(float x, float d, float t0, float c, float kb, int power,
+                                         const float (&al)[kLsMaxPts], int m, float (&s)[kLsMaxPts],
+                                         float (&e)[kLsMaxPts]) {
+    const float inv = __frcp_rn(c);
+    const float bc = t0 * kb * c;                  // t0 beta c / (p + 1)
+#pragma unroll
+    for (int k = 0; k < kLsMaxPts; k++) {
+        if (k < m) {
+            const float v = fmaf(al[k], d, x);
+            const float w = pow_p1<PW>(v * inv, power);
+            two_sum_add(s[k], e[k], fmaf(bc, w, t0 * v));
+        }
+    }
+}
+
+template <bool VEC, int PW>
+__global__ void __launch_bounds__(kPhiThreads, 2) k_phi(PhiArgs a) {
+    __shared__ double s_w[kPhiThreads / 32][kLsMaxPts];
+    __shared__ bool s_last;
+    const int m = a.m;
+    float al[kLsMaxPts], s[kLsMaxPts], e[kLsMaxPts];
+#pragma unroll
+    for (int k = 0; k < kLsMaxPts; k++) {
+        al[k] = k < m ? (float)a.pts[k] : 0.f;
+        s[k] = 0.f;
+        e[k] = 0.f;
+    }
+    const float kb = a.beta / (float)(a.power + 1);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t done = 0;
+    if (VEC) {
+        const int64_t n4 = a.n / 4;
+        const float4* x4 = reinterpret_cast<const float4*>(a.x);
+        const float4* d4 = reinterpret_cast<const float4*>(a.d);
+        const float4* t4 = reinterpret_cast<const float4*>(a.t0);
+        const float4* c4 = reinterpret_cast<const float4*>(a.c);
+        // two strides' loads in flight (128 bytes per thread) before the arithmetic
+        int64_t i = tid;
+        for (; i + stride < n4; i += 2 * stride) {
+            const float4 X = __ldcs(x4 + i), D = __ldcs(d4 + i), T = __ldcs(t4 + i), C = __ldcs(c4 + i);
+            const float4 X2 = __ldcs(x4 + i + stride), D2 = __ldcs(d4 + i + stride), T2 = __ldcs(t4 + i + stride),
+                         C2 = __ldcs(c4 + i + stride);
+            phi_link<PW>(X.x, D.x, T.x, C.x, kb, a.power, al, m, s, e);
+            phi_link<PW>(X.y, D.y, T.y, C.y, kb, a.power, al, m, s, e);
+            phi_link<PW>(X.z, D.z, T.z, C.z, kb, a.power, al, m, s, e);
+            phi_link<PW>(X.w, D.w, T.w, C.w, kb, a.power, al, m, s, e);
+            phi_link<PW>(X2.x, D2.x, T2.x, C2.x, kb, a.power, al, m, s, e);
+            phi_link<PW>(X2.y, D2.y, T2.y, C2.y, kb, a.power, al, m, s, e);
+            phi_link<PW>(X2.z, D2.z, T2.z, C2.z, kb, a.power, al, m, s, e);
+            phi_link<PW>(X2.w, D2.w, T2.w, C2.w, kb, a.power, al, m, s, e);
+        }
+        if (i < n4) {
+            const float4 X = __ldcs(x4 + i), D = __ldcs(d4 + i), T = __ldcs(t4 + i), C = __ldcs(c4 + i);
+            phi_link<PW>(X.x, D.x, T.x, C.x, kb, a.power, al, m, s, e);
+            phi_link<PW>(X.y, D.y, T.y, C.y, kb, a.power, al, m, s, e);
+            phi_link<PW>(X.z, D.z, T.z, C.z, kb, a.power, al, m, s, e);
+            phi_link<PW>(X.w, D.w, T.w, C.w, kb, a.power, al, m, s, e);
+        }
+        done = n4 * 4;
+    }
+    for (int64_t i = done + tid; i < a.n; i += stride)
+        phi_link<PW>(__ldcs(a.x + i), __ldcs(a.d + i), __ldcs(a.t0 + i), __ldcs(a.c + i), kb, a.power, al, m, s, e);
+
+    // per point: thread pair -> float64, warp butterfly, warps in order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kLsMaxPts; k++) {
+        if (k < m) {
+            double v = (double)s[k] + (double)e[k];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s_w[warp][k] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        double v = 0.0;
+        for (int w = 0; w < kPhiThreads / 32; w++) v += s_w[w][threadIdx.x];
+        a.partials[(int64_t)blockIdx.x * kLsMaxPts + threadIdx.x] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last block: warp w sums points w, w + 8, ... over the blocks, lanes
+    // striding the block index, then a butterfly (a fixed order per grid)
+    for (int k = warp; k < m; k += kPhiThreads / 32) {
+        double v = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(a.partials + (int64_t)b * kLsMaxPts + k);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) a.out[k] = v;
+    }
+    if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+// ---- search state ----------------------------------------------------------
+
+// F_0 = F_1 = 1, F_k = F_{k-1} + F_{k-2} (exact in float64 up to F_78)
+__device__ double fib(int k) {
+    double a = 1.0, b = 1.0;
+    for (int i = 1; i < k; i++) {
+        const double t = __dadd_rn(a, b);
+        a = b;
+        b = t;
+    }
+    return b;
+}
+
+struct LsNode {
+    double a, b, x1, x2;
+    int j;     // iterations done
+};
+
+// The child of n after one comparison: br 0 (x1 better) keeps [a, x2] and
+// moves x1 up to x2; br 1 keeps [x1, b] and moves x2 down to x1.  Returns
+// the new point the child needs.
+__device__ double ls_child(const LsState& s, const LsNode& n, int br, LsNode& c) {
+    c = n;
+    c.j = n.j + 1;
+    if (s.method == 0) {
+        if (br == 0) {
+            c.b = n.x2;
+            c.x2 = n.x1;
+            c.x1 = __dsub_rn(c.b, __dmul_rn(s.golden, __dsub_rn(c.b, c.a)));
+            return c.x1;
+        }
+        c.a = n.x1;
+        c.x1 = n.x2;
+        c.x2 = __dadd_rn(c.a, __dmul_rn(s.golden, __dsub_rn(c.b, c.a)));
+        return c.x2;
+    }
+    const int N = s.count, j = c.j;
+    const bool last = j == N - 2;
+    if (br == 0) {
+        c.b = n.x2;
+        c.x2 = n.x1;
+        c.x1 = last ? __dsub_rn(c.x2, __dmul_rn(0.1, s.u)) : __dadd_rn(c.a, __dmul_rn(fib(N - j - 2), s.u));
+        return c.x1;
+    }
+    c.a = n.x1;
+    c.x1 = n.x2;
+    c.x2 = last ? __dadd_rn(c.x1, __dmul_rn(0.1, s.u)) : __dadd_rn(c.a, __dmul_rn(fib(N - j - 1), s.u));
+    return c.x2;
+}
+
+// The tree of the next `levels` iterations below root, into pts[base...]
+__device__ int ls_tree(LsState& s, const LsNode& root, int levels, int base) {
+    LsNode cur[1 << kLsMaxDepth], nxt[1 << kLsMaxDepth];
+    cur[0] = root;
+    int width = 1, np = 0;
+    for (int l = 1; l <= levels; l++) {
+        for (int k = 0; k < width; k++)
+            for (int br = 0; br < 2; br++) s.pts[base + np++] = ls_child(s, cur[k], br, nxt[2 * k + br]);
+        width *= 2;
+        for (int k = 0; k < width; k++) cur[k] = nxt[k];
+    }
+    return np;
+}
+
+__global__ void k_ls_init(LsState* sp, double lo, double hi, int method, int count, int total, int depth) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    LsState& s = *sp;
+    s.method = method;
+    s.count = count;
+    s.total = total;
+    s.depth = depth;
+    s.iter = 0;
+    s.first = 1;
+    s.done = 0;
+    s.golden = __ddiv_rn(__dsub_rn(sqrt(5.0), 1.0), 2.0);
+    s.a = lo;
+    s.b = hi;
+    if (method == 0) {
+        s.u = 0.0;
+        s.x1 = __dsub_rn(hi, __dmul_rn(s.golden, __dsub_rn(hi, lo)));
+        s.x2 = __dadd_rn(lo, __dmul_rn(s.golden, __dsub_rn(hi, lo)));
+    } else {
+        s.u = __ddiv_rn(__dsub_rn(hi, lo), fib(count));
+        s.x1 = __dadd_rn(lo, __dmul_rn(fib(count - 2), s.u));
+        s.x2 = __dadd_rn(lo, __dmul_rn(fib(count - 1), s.u));
+    }
+    s.pts[0] = s.x1;
+    s.pts[1] = s.x2;
+    const LsNode root{s.a, s.b, s.x1, s.x2, 0};
+    s.npts = 2 + ls_tree(s, root, depth < total ? depth : total, 2);
+}
+
+// result: a, b, the better of the last two points and its value
+__global__ void k_ls_update(LsState* sp, double* result) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    LsState& s = *sp;
+    if (s.done) return;
+    const int base = s.first ? 2 : 0;
+    if (s.first) {
+        s.f1 = s.vals[0];
+        s.f2 = s.vals[1];
+    }
+    LsNode n{s.a, s.b, s.x1, s.x2, s.iter};
+    int path = 0;
+    for (int l = 0; l < s.depth && s.iter < s.total; l++) {
+        const int br = s.f1 < s.f2 ? 0 : 1;
+        LsNode c;
+        ls_child(s, n, br, c);
+        path = 2 * path + br;
+        const double fnew = s.vals[base + (2 << l) - 2 + path];
+        if (br == 0) {
+            s.f2 = s.f1;
+            s.f1 = fnew;
+        } else {
+            s.f1 = s.f2;
+            s.f2 = fnew;
+        }
+        n = c;
+        s.iter++;
+    }
+    s.a = n.a;
+    s.b = n.b;
+    s.x1 = n.x1;
+    s.x2 = n.x2;
+    s.first = 0;
+    if (s.iter < s.total) {
+        const int left = s.total - s.iter;
+        s.npts = ls_tree(s, n, s.depth < left ? s.depth : left, 0);
+        return;
+    }
+    // finished: Fibonacci's last comparison only shrinks the bracket
+    if (s.method == 1) {
+        if (s.f1 < s.f2) s.b = s.x2;
+        else s.a = s.x1;
+    }
+    s.done = 1;
+    s.npts = 0;
+    result[0] = s.a;
+    result[1] = s.b;
+    result[2] = s.f1 < s.f2 ? s.x1 : s.x2;
+    result[3] = s.f1 < s.f2 ? s.f1 : s.f2;
+}
+
+// ---- launchers -------------------------------------------------------------
+
+template <bool VEC>
+static const void* phi_fn(int power) {
+    switch (power) {
+        case 1: return reinterpret_cast<const void*>(&k_phi<VEC, 1>);
+        case 2: return reinterpret_cast<const void*>(&k_phi<VEC, 2>);
+        case 3: return reinterpret_cast<const void*>(&k_phi<VEC, 3>);
+        case 4: return reinterpret_cast<const void*>(&k_phi<VEC, 4>);
+        default: return reinterpret_cast<const void*>(&k_phi<VEC, 0>);
+    }
+}
+
+const void* phi_kernel(bool vec, int power) { return vec ? phi_fn<true>(power) : phi_fn<false>(power); }
+
+template <bool VEC>
+static void phi_go(const PhiArgs& a, int grid, cudaStream_t st) {
+    switch (a.power) {
+        case 1: k_phi<VEC, 1><<<grid, kPhiThreads, 0, st>>>(a); break;
+        case 2: k_phi<VEC, 2><<<grid, kPhiThreads, 0, st>>>(a); break;
+        case 3: k_phi<VEC, 3><<<grid, kPhiThreads, 0, st>>>(a); break;
+        case 4: k_phi<VEC, 4><<<grid, kPhiThreads, 0, st>>>(a); break;
+        default: k_phi<VEC, 0><<<grid, kPhiThreads, 0, st>>>(a); break;
+    }
+}
+
+cudaError_t launch_phi(const PhiArgs& a, int grid, bool vec, cudaStream_t st) {
+    if (vec) phi_go<true>(a, grid, st);
+    else phi_go<false>(a, grid, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ls_init(LsState* s, double lo, double hi, int method, int count, int total, int depth,
+                           cudaStream_t st) {
+    k_ls_init<<<1, 32, 0, st>>>(s, lo, hi, method, count, total, depth);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ls_update(LsState* s, double* result, cudaStream_t st) {
+    k_ls_update<<<1, 32, 0, st>>>(s, result);
+    return cudaGetLastError();
+}
+
+}  // namespace pr

@@ -58,6 +58,9 @@ _SIGS = {
     "pr_reduce_axis": [_P, _I64, _I64, _I64, _I, _I, _I, _P, _P, _P, _P],
     "pr_scan": [_P, _I64, _I, _I, ctypes.c_int32, _P, _P],
     "pr_check_bounded_wait": [ctypes.c_int32, _P],
+    "pr_beckmann": [_P, _P, _P, _P, _I64, ctypes.c_float, _I32, _P, _I32, _P, _P],
+    "pr_line_search": [_P, _P, _P, _P, _I64, ctypes.c_float, _I32, ctypes.c_double, ctypes.c_double, _I, _I32,
+                       _I32, _P, _P],
     "pr_reduce_axis_backward": [_I, _I, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P],
     "pr_reduce_host": [_P, _I64, _I, _I, _P, _P],
     "pr_reduce_noalloc": [_P, _I64, _I, _I, _P, _P],
@@ -156,6 +159,14 @@ def pr_scan(x, n, dtype, op, exclusive, y, stream):
 
 def pr_check_bounded_wait(polls, stream):
     return lib().pr_check_bounded_wait(polls, stream)
+
+
+def pr_beckmann(x, d, t0, cap, n, beta, power, alphas, m, out, stream):
+    return lib().pr_beckmann(x, d, t0, cap, n, beta, power, alphas, m, out, stream)
+
+
+def pr_line_search(x, d, t0, cap, n, beta, power, lo, hi, method, count, depth, result, stream):
+    return lib().pr_line_search(x, d, t0, cap, n, beta, power, lo, hi, method, count, depth, result, stream)
 
 
 def pr_reduce_host(host_x, n, dtype, op, host_out, stream):
@@ -345,6 +356,56 @@ def scan(x, op: str, exclusive: bool = False, out=None, stream=None):
     y = out if out is not None else torch.empty(x.shape, dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
     check(pr_scan(_ptr(x), x.numel(), DTYPES[d], OPS[op], 1 if exclusive else 0, _ptr(y), _stream(x, stream)))
     return y
+
+
+SEARCH = {"golden": 0, "fibonacci": 1}
+GOLDEN_RATIO_R = (5.0 ** 0.5 - 1.0) / 2.0
+
+
+def _links(x, d, t0, cap):
+    torch = _torch()
+    for t in (x, d, t0, cap):
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != x.numel():
+            raise ValueError("x, d, t0, cap: contiguous float32 CUDA tensors of one length")
+
+
+def beckmann(x, d, t0, cap, alphas, beta: float = 0.15, power: int = 4, stream=None):
+    """phi(alpha) of the Beckmann objective at each alpha (at most 16), one
+    pass over the links; a float64 CUDA tensor."""
+    torch = _torch()
+    _links(x, d, t0, cap)
+    al = torch.as_tensor(alphas, dtype=torch.float64).reshape(-1).to(x.device)
+    out = torch.empty(al.numel(), dtype=torch.float64, device=x.device)
+    check(pr_beckmann(_ptr(x), _ptr(d), _ptr(t0), _ptr(cap), x.numel(), beta, power, _ptr(al), al.numel(),
+                      _ptr(out), _stream(x, stream)))
+    return out
+
+
+def golden_iterations(lo: float, hi: float, tol: float) -> int:
+    """Golden-section iterations until the bracket is at most tol wide."""
+    import math
+    if hi - lo <= tol:
+        return 0
+    return int(math.ceil(math.log(tol / (hi - lo)) / math.log(GOLDEN_RATIO_R) - 1e-12))
+
+
+def line_search(x, d, t0, cap, lo: float = 0.0, hi: float = 1.0, beta: float = 0.15, power: int = 4,
+                method: str = "golden", tol: float | None = None, count: int | None = None, depth: int = 2,
+                result=None, stream=None):
+    """Minimise the Beckmann objective on [lo, hi] by golden-section (count
+    iterations, or enough for a bracket of width tol) or Fibonacci search
+    (count evaluations).  Returns a float64 CUDA tensor: final a, b, the
+    better of the last two points, its phi."""
+    torch = _torch()
+    _links(x, d, t0, cap)
+    if count is None:
+        if method != "golden" or tol is None:
+            raise ValueError("give count, or tol for golden-section search")
+        count = golden_iterations(lo, hi, tol)
+    res = result if result is not None else torch.empty(4, dtype=torch.float64, device=x.device)
+    check(pr_line_search(_ptr(x), _ptr(d), _ptr(t0), _ptr(cap), x.numel(), beta, power, lo, hi, SEARCH[method],
+                         count, depth, _ptr(res), _stream(x, stream)))
+    return res
 
 
 def axis_shape(shape, dim):

@@ -16,6 +16,10 @@ Section 4):
                  fp32 N(0,1) values
   differentiation: [64, 2^20] fp32 N(0,1); product rows U[0.5,1.5) with 1 %
                  exact zeros
+  line search:   a road network's links: capacities U[500, 4000), free-flow
+                 times U[0.5, 5), flows x = c U[0.2, 1.5), an all-or-nothing
+                 auxiliary flow y (30 % of links loaded with c U[0, 3), the
+                 rest 0) and the direction d = y - x
 """
 from __future__ import annotations
 
@@ -148,3 +152,14 @@ def plant(x: np.ndarray, idx: int, value) -> np.ndarray:
     y = np.array(x, copy=True)
     y.reshape(-1)[idx] = value
     return y
+
+
+def network_links(n: int, seed: int):
+    """float32 (x, d, t0, c) of n links: flows, direction y - x, free-flow
+    times and capacities of a Frank-Wolfe step (see the module docstring)."""
+    rng = _rng(seed)
+    c = rng.uniform(500.0, 4000.0, n).astype(np.float32)
+    t0 = rng.uniform(0.5, 5.0, n).astype(np.float32)
+    x = (c * rng.uniform(0.2, 1.5, n)).astype(np.float32)
+    y = np.where(rng.uniform(size=n) < 0.3, c * rng.uniform(0.0, 3.0, n), 0.0).astype(np.float32)
+    return x, (y - x).astype(np.float32), t0, c

@@ -179,3 +179,31 @@ def test_valid_call_without_a_gpu_fails_loudly(L):
     assert pr.pr_reduce(FAKE, 10, F32, SUM, FAKE, None) == CUDA
     with pytest.raises(pr.PrError):
         pr.check(pr.pr_reduce(FAKE, 10, F32, SUM, FAKE, None))
+
+
+def test_line_search_rejections():
+    """Argument checks of pr_beckmann and pr_line_search (all on the host)."""
+    F = FAKE
+    ok = (F, F, F, F, 100, 0.15, 4)
+    assert pr.pr_beckmann(F, F, F, F, -1, 0.15, 4, F, 2, F, None) == INVALID
+    assert pr.pr_beckmann(None, F, F, F, 100, 0.15, 4, F, 2, F, None) == INVALID
+    assert pr.pr_beckmann(F + 2, F, F, F, 100, 0.15, 4, F, 2, F, None) == INVALID      # 4-byte alignment
+    assert pr.pr_beckmann(F, F, F, F, 100, -1.0, 4, F, 2, F, None) == INVALID          # beta < 0
+    assert pr.pr_beckmann(F, F, F, F, 100, float("nan"), 4, F, 2, F, None) == INVALID
+    assert pr.pr_beckmann(F, F, F, F, 100, 0.15, 0, F, 2, F, None) == INVALID          # power
+    assert pr.pr_beckmann(F, F, F, F, 100, 0.15, 17, F, 2, F, None) == INVALID
+    assert pr.pr_beckmann(*ok, F, 0, F, None) == INVALID                                # m
+    assert pr.pr_beckmann(*ok, F, 17, F, None) == INVALID
+    assert pr.pr_beckmann(*ok, None, 2, F, None) == INVALID
+    assert pr.pr_beckmann(*ok, F + 4, 2, F, None) == INVALID                            # 8-byte alignment
+    assert pr.pr_line_search(*ok, 1.0, 1.0, 0, 10, 2, F, None) == INVALID               # lo < hi
+    assert pr.pr_line_search(*ok, 0.0, float("inf"), 0, 10, 2, F, None) == INVALID
+    assert pr.pr_line_search(*ok, 0.0, 1.0, 2, 10, 2, F, None) == INVALID               # method
+    assert pr.pr_line_search(*ok, 0.0, 1.0, 0, -1, 2, F, None) == INVALID              # golden iterations
+    assert pr.pr_line_search(*ok, 0.0, 1.0, 0, 201, 2, F, None) == INVALID
+    assert pr.pr_line_search(*ok, 0.0, 1.0, 1, 2, 2, F, None) == INVALID               # Fibonacci evaluations
+    assert pr.pr_line_search(*ok, 0.0, 1.0, 1, 79, 2, F, None) == INVALID
+    assert pr.pr_line_search(*ok, 0.0, 1.0, 0, 10, 0, F, None) == INVALID              # depth
+    assert pr.pr_line_search(*ok, 0.0, 1.0, 0, 10, 4, F, None) == INVALID
+    assert pr.pr_line_search(*ok, 0.0, 1.0, 0, 10, 2, None, None) == INVALID
+    assert pr.pr_line_search(*ok, 0.0, 1.0, 0, 10, 2, F + 4, None) == INVALID

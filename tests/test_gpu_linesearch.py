@@ -1,0 +1,183 @@
+"""Parity of the line search on the reduction (golden-section and Fibonacci
+search of the Beckmann objective) with the oracle: every evaluation within
+its error bound, the same sequence of points as the one-by-one search
+whatever the speculation depth, the oracle's bracket wherever every
+comparison is decided by more than the evaluation error, and convergence to
+the minimiser otherwise."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import linesearch as ols
+from paper_1710_07358_gb300 import pr, synth
+
+pytestmark = pytest.mark.gpu
+
+BETA = 0.15
+
+
+def dev(arrs, offset=0):
+    """CUDA float32 copies, `offset` elements past a 16-byte boundary."""
+    import torch
+    out = []
+    for a in arrs:
+        buf = torch.zeros(a.size + offset, dtype=torch.float32, device="cuda")
+        buf[offset:] = torch.from_numpy(a).cuda()
+        out.append(buf[offset:])
+    return out
+
+
+def abs_terms(arrs, p, alpha):
+    return math.fsum(np.abs(ols.phi_terms(*arrs, BETA, p, alpha)).tolist())
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 7, 1000, 100003, (1 << 20) + 5])
+@pytest.mark.parametrize("p", [1, 4, 6])
+def test_evaluation_within_bound(n, p):
+    arrs = synth.network_links(n, 10 + n % 97)
+    alphas = np.array([0.0, 0.125, 0.3, 0.5, 0.77, 1.0, 2.5], dtype=np.float64)
+    got = pr.beckmann(*dev(arrs), alphas, BETA, p).cpu().numpy()
+    for k, al in enumerate(alphas):
+        a32 = float(np.float32(al))                       # the kernel evaluates at float32(alpha)
+        want = ols.phi(*arrs, BETA, p, a32)
+        bound = (p + 6) * 2.0 ** -24 * abs_terms(arrs, p, a32) + 1e-300
+        assert abs(got[k] - want) <= bound, (n, p, al, got[k], want, bound)
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_evaluation_unaligned_and_sixteen_points(offset):
+    arrs = synth.network_links(50021, 20 + offset)
+    alphas = np.linspace(0.0, 1.0, 16)
+    got = pr.beckmann(*dev(arrs, offset), alphas, BETA, 4).cpu().numpy()
+    aligned = pr.beckmann(*dev(arrs), alphas, BETA, 4).cpu().numpy()
+    for k, al in enumerate(alphas):
+        want = ols.phi(*arrs, BETA, 4, float(np.float32(al)))
+        bound = 10 * 2.0 ** -24 * abs_terms(arrs, 4, float(np.float32(al)))
+        assert abs(got[k] - want) <= bound and abs(aligned[k] - want) <= bound
+
+
+def test_evaluation_at_the_benchmark_size():
+    n = 1 << 24
+    arrs = synth.network_links(n, synth.config_seed(7))
+    alphas = np.array([0.25, 0.6], dtype=np.float64)
+    got = pr.beckmann(*dev(arrs), alphas, BETA, 4).cpu().numpy()
+    for k, al in enumerate(alphas):
+        want = ols.phi(*arrs, BETA, 4, float(np.float32(al)))
+        assert abs(got[k] - want) <= 8 * 2.0 ** -24 * abs_terms(arrs, 4, float(np.float32(al)))
+
+
+def gpu_search(arrs, p, lo, hi, method, count, depth, offset=0):
+    r = pr.line_search(*dev(arrs, offset), lo=lo, hi=hi, beta=BETA, power=p, method=method, count=count,
+                       depth=depth)
+    return r.cpu().numpy()
+
+
+def oracle_search(arrs, p, lo, hi, method, count):
+    f = lambda al: ols.phi(*arrs, BETA, p, float(np.float32(al)))
+    if method == "golden":
+        return ols.golden_section(f, lo, hi, count)
+    return ols.fibonacci_search(f, lo, hi, count)
+
+
+def min_margin(ev, arrs, p, method):
+    """Smallest |f1 - f2| / sum|terms| over the comparisons the search made
+    (replayed from its evaluation list; Fibonacci also compares the last two
+    points to shrink its final bracket)."""
+    scale = max(abs_terms(arrs, p, x) for x, _ in ev)
+    worst = math.inf
+    (x1, f1), (x2, f2) = ev[0], ev[1]
+    for xn, fn in ev[2:]:
+        worst = min(worst, abs(f1 - f2) / scale)
+        if f1 < f2:
+            x2, f2 = x1, f1
+            x1, f1 = xn, fn
+        else:
+            x1, f1 = x2, f2
+            x2, f2 = xn, fn
+    if method == "fibonacci":
+        worst = min(worst, abs(f1 - f2) / scale)
+    return worst
+
+
+@pytest.mark.parametrize("method,count", [("golden", 10), ("golden", 0), ("golden", 1), ("fibonacci", 3),
+                                          ("fibonacci", 10)])
+@pytest.mark.parametrize("p,hi", [(1, 4.0), (4, 1.0)])
+def test_search_matches_oracle_exactly(method, count, p, hi):
+    arrs = synth.network_links(30011, 31 + p)
+    a, b, ev = oracle_search(arrs, p, 0.0, hi, method, count)
+    # every comparison decided by more than twice the two evaluations' error
+    # bound: the kernel must take the same branches, place the same float64
+    # points and end with the same bracket, bit for bit
+    assert min_margin(ev, arrs, p, method) > 4 * (p + 6) * 2.0 ** -24
+    for depth in (1, 2, 3):
+        got = gpu_search(arrs, p, 0.0, hi, method, count, depth)
+        assert got[0] == a and got[1] == b, (depth, got[:2], (a, b))
+        assert got[2] in [x for x, _ in ev] and a <= got[2] <= b
+        want_f = ols.phi(*arrs, BETA, p, float(np.float32(got[2])))
+        assert abs(got[3] - want_f) <= (p + 6) * 2.0 ** -24 * abs_terms(arrs, p, float(np.float32(got[2])))
+
+
+@pytest.mark.parametrize("method,count", [("golden", 40), ("fibonacci", 40)])
+@pytest.mark.parametrize("p", [1, 4])
+def test_search_converges_to_the_minimiser(method, count, p):
+    arrs = synth.network_links(20011, 41 + p)
+    hi = 4.0 if p == 1 else 1.0
+    got = gpu_search(arrs, p, 0.0, hi, method, count, 2)
+    a, b = got[0], got[1]
+    if p == 1:
+        star = ols.quadratic_minimizer(*arrs, BETA)
+    else:
+        f = lambda al: ols.phi(*arrs, BETA, p, al)
+        oa, ob, _ = ols.golden_section(f, 0.0, hi, 60)
+        star = (oa + ob) / 2
+    # where phi is flat to within the evaluation error, any point is as good:
+    # |phi(s + w) - phi(s)| ~ phi''(s) w^2 / 2 = eps sum|terms|
+    h = 1e-3
+    f2 = (ols.phi(*arrs, BETA, p, star + h) - 2 * ols.phi(*arrs, BETA, p, star) + ols.phi(*arrs, BETA, p, star - h)) / h**2
+    eps = (p + 6) * 2.0 ** -24 * abs_terms(arrs, p, star)
+    flat = math.sqrt(2 * eps / f2)
+    assert a - flat - 1e-9 <= star <= b + flat + 1e-9, (a, b, star, flat)
+    assert b - a <= (hi * ols.GOLDEN ** count if method == "golden" else 1.1 * hi / ols.fibonacci(count)) * (1 + 1e-9)
+
+
+def test_depth_and_alignment_do_not_change_the_search():
+    arrs = synth.network_links(70001, 51)
+    ref = gpu_search(arrs, 4, 0.0, 1.0, "golden", 35, 1)
+    for depth in (2, 3):
+        assert np.array_equal(gpu_search(arrs, 4, 0.0, 1.0, "golden", 35, depth), ref)
+    # unaligned arrays take the scalar loads: a different float32 evaluation
+    # order per thread, so only the bracket's convergence is compared
+    un = gpu_search(arrs, 4, 0.0, 1.0, "golden", 35, 2, offset=1)
+    assert abs((un[0] + un[1]) - (ref[0] + ref[1])) / 2 <= 1e-3
+
+
+def test_monotone_objective_ends_at_the_lower_end():
+    x, d, t0, c = synth.network_links(10007, 61)
+    d = np.abs(d)                                     # every link only gains flow: phi increases
+    got = gpu_search((x, d, t0, c), 4, 0.0, 1.0, "golden", 30, 2)
+    assert got[0] == 0.0 and got[1] <= ols.GOLDEN ** 30 * (1 + 1e-9)
+
+
+def test_no_links_and_graph_replay():
+    import torch
+    e = [np.zeros(0, dtype=np.float32)] * 4
+    got = gpu_search(e, 4, 0.0, 1.0, "golden", 5, 2)       # phi = 0: every comparison a tie
+    a, b, _ = ols.golden_section(lambda al: 0.0, 0.0, 1.0, 5)
+    assert got[0] == a and got[1] == b and got[3] == 0.0
+    arrs = dev(synth.network_links(40009, 71))
+    s = torch.cuda.Stream()
+    res = torch.empty(4, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(s):
+        pr.line_search(*arrs, method="fibonacci", count=20, depth=3, result=res, stream=s)
+    s.synchronize()
+    want = res.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pr.line_search(*arrs, method="fibonacci", count=20, depth=3, result=res, stream=s)
+    for _ in range(3):
+        res.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(res, want)
+    assert pr.last_device_error() == 0
