@@ -14,8 +14,9 @@ Also reported in the same line:
                segmented form (4096 log-uniform segments, autotuned, replayed from a
                CUDA graph), forward+backward of [64, 2^20] row reductions, and
                reductions of a non-last axis (1 GiB: middle axis of [16, 4096,
-               4096] with its gradient, first axis of [16384, 16384]), and one-pass
-               prefix scans of 2^28 elements.
+               4096] with its gradient, first axis of [16384, 16384]), one-pass
+               prefix scans of 2^28 elements, and golden-section / Fibonacci line
+               searches of the Beckmann objective over 2^24 links.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms]
 
@@ -168,7 +169,7 @@ def cpu_oracle_sum(x):
 # Secondary forms (all on the same GPU, same run)
 # --------------------------------------------------------------------------
 
-FORM_GROUPS = ("plain", "precision", "illcond", "segmented", "fwdbwd", "axis", "scan")
+FORM_GROUPS = ("plain", "precision", "illcond", "segmented", "fwdbwd", "axis", "scan", "linesearch")
 
 
 def forms(steps, warmup, peak, only=None, tune=True):
@@ -232,6 +233,8 @@ def forms(steps, warmup, peak, only=None, tune=True):
         axis(res, k, warmup, peak, st, g)
     if "scan" in want:
         scan(res, k, warmup, peak, st, g)
+    if "linesearch" in want:
+        linesearch(res, k, warmup, peak, st, g)
     return res
 
 
@@ -265,6 +268,48 @@ def scan(res, k, warmup, peak, st, g):
     _, per = time_launches(lambda: pr.scan(xf, "max", out=yf), k, warmup, st)
     put("scan_f32_max", per, 2 * n * 4)
     del xf, yf, xi
+
+
+def linesearch(res, k, warmup, peak, st, g):
+    """Golden-section (tolerance 1e-6 on [0, 1]: 29 iterations) and Fibonacci
+    (31 evaluations) search of the Beckmann objective (BPR, beta 0.15, power
+    4) over 2^24 synthetic links: four float32 arrays, 256 MiB per pass, more
+    than L2 holds.  depth D decides D iterations per pass over the links.
+    GB/s counts 16 bytes per link and pass; one evaluation pass alone is timed
+    with 2 and 6 points."""
+    import torch
+    from paper_1710_07358_gb300 import pr
+    dev = torch.device("cuda")
+    n = 1 << 24
+    g.manual_seed(synth.config_seed(7))
+    u = lambda lo, hi: torch.rand(n, generator=g, device=dev) * (hi - lo) + lo
+    c = u(500.0, 4000.0)
+    t0 = u(0.5, 5.0)
+    x = c * u(0.2, 1.5)
+    y = torch.where(torch.rand(n, generator=g, device=dev) < 0.3, c * u(0.0, 3.0), torch.zeros_like(c))
+    d = y - x
+    del y
+    nb = 16 * n
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    iters = pr.golden_iterations(0.0, 1.0, 1e-6)
+    for method, count in (("golden", iters), ("fibonacci", 31)):
+        total = count if method == "golden" else count - 2
+        for depth in (1, 2, 3):
+            passes = max(1, -(-total // depth))
+            _, per = time_launches(lambda: pr.line_search(x, d, t0, c, method=method, count=count, depth=depth,
+                                                          result=out), k, warmup, st)
+            res["linesearch_%s_d%d" % (method, depth)] = {
+                "us": round(per * 1e3, 1), "passes": passes, "GB/s": round(gbs(nb * passes, per), 1),
+                "frac": round(gbs(nb * passes, per) / peak, 4), "alpha": round(float(out[2].item()), 7)}
+    for m in (2, 6):
+        al = torch.linspace(0.1, 0.9, m, dtype=torch.float64, device=dev)
+        ph = torch.empty(m, dtype=torch.float64, device=dev)
+        _, per = time_launches(lambda: pr.check(pr.pr_beckmann(x.data_ptr(), d.data_ptr(), t0.data_ptr(),
+                                                               c.data_ptr(), n, 0.15, 4, al.data_ptr(), m,
+                                                               ph.data_ptr(), st.cuda_stream)), k, warmup, st)
+        res["beckmann_pass_%dpts" % m] = {"us": round(per * 1e3, 2), "GB/s": round(gbs(nb, per), 1),
+                                          "frac": round(gbs(nb, per) / peak, 4)}
+    del x, d, t0, c
 
 
 def axis(res, k, warmup, peak, st, g):
