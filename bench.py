@@ -278,7 +278,7 @@ def linesearch(res, k, warmup, peak, st, g):
     GB/s counts 16 bytes per link and pass; one evaluation pass alone is timed
     with 2 and 6 points."""
     import torch
-    from paper_1710_07358_gb300 import pr
+    from paper_1710_07358_gb300 import pr, synth
     dev = torch.device("cuda")
     n = 1 << 24
     g.manual_seed(synth.config_seed(7))
