@@ -235,9 +235,10 @@ pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream);
  *   v_i = x[i] + alpha d[i].
  * x (flows), d (direction), t0 (free-flow times), cap (capacities > 0): n
  * float32 each, device memory, 4-byte aligned (16-byte aligned: vector
- * loads).  beta >= 0, power in [1, 16].  Terms are evaluated in float32 and
- * summed per point with TwoSum, then combined in float64 in a fixed order:
- * deterministic, within about (power + 4) 2^-24 sum |term| of the exact sum.
+ * loads).  beta >= 0, power in [1, 16].  Terms are evaluated in float32, a
+ * thread's links summed pairwise per point into a Kahan (sum, compensation)
+ * pair, then combined in float64 in a fixed order: deterministic, within
+ * (power + 13) 2^-24 sum |term| of the exact sum of the terms.
  *
  * pr_beckmann: out[k] = phi(alphas[k]) for k < m, m in [1, 16], in one pass
  * over the links (alphas and out: device, 8-byte aligned; alphas rounded to

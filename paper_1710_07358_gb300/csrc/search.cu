@@ -7,10 +7,11 @@
 //   v_i = x_i + alpha d_i.
 //
 // k_phi      one pass over the four float32 link arrays evaluates phi at up
-//            to kLsMaxPts points: each term in float32, accumulated per point
-//            with TwoSum (error-free) into (sum, compensation) pairs, combined
-//            per block in float64 and by the last block in block order (the
-//            persistent reduction of Section 3 with a fixed combine order).
+//            to kLsMaxPts points: each term in float32, a thread's eight
+//            links per point summed pairwise and added to the point's Kahan
+//            pair, combined per block in float64 and by the last block in
+//            block order (the persistent reduction of Section 3 with a fixed
+//            combine order).  Error: within (p + 13) 2^-24 sum |term|.
 // k_ls_init  places the first two points and the speculative tree.
 // k_ls_update walks depth D decisions with the values of the pass, then places
 //            the next pass's tree: the 2^(D+1) - 2 points the next D
@@ -28,42 +29,63 @@ namespace pr {
 
 // ---- evaluation pass -------------------------------------------------------
 
-__device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
-    const float t = s + v;
-    const float bp = t - s;
-    const float ap = t - bp;
-    c = c + ((s - ap) + (v - bp));
+// Kahan's compensated add: c holds the negated low part lost so far, so the
+// running sum is s - c
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
     s = t;
 }
 
-// (v / c)^(p + 1) by repeated squaring for the usual powers
+// (v / c)^(p + 1) by repeated squaring for the usual power
 template <int PW>
 __device__ __forceinline__ float pow_p1(float q, int power) {
-    if constexpr (PW == 1) return q * q;
-    else if constexpr (PW == 2) return (q * q) * q;
-    else if constexpr (PW == 3) { const float q2 = q * q; return q2 * q2; }
-    else if constexpr (PW == 4) { const float q2 = q * q; return (q2 * q2) * q; }
-    else {
+    if constexpr (PW == 4) {
+        const float q2 = q * q;
+        return (q2 * q2) * q;
+    } else {
         float r = q;
         for (int k = 0; k < power; k++) r *= q;
         return r;
     }
 }
 
-template <int PW>
-__device__ __forceinline__ void phi_link(float x, float d, float t0, float c, float kb, int power,
-                                         const float (&al)[kLsMaxPts], int m, float (&s)[kLsMaxPts],
-                                         float (&e)[kLsMaxPts]) {
-    const float inv = __frcp_rn(c);
-    const float bc = t0 * kb * c;                  // t0 beta c / (p + 1)
+// L links of this thread at the first m points: per point the L terms are
+// summed pairwise in float32 and the sum enters the point's Kahan pair (the
+// loop over points stops at m, so a pass costs what its points need)
+template <int PW, int L>
+__device__ __forceinline__ void phi_group(const float (&X)[L], const float (&D)[L], const float (&T)[L],
+                                          const float (&C)[L], float kb, int power, const float (&al)[kLsMaxPts],
+                                          int m, float (&s)[kLsMaxPts], float (&e)[kLsMaxPts]) {
+    float inv[L], bc[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        inv[l] = __frcp_rn(C[l]);
+        bc[l] = T[l] * kb * C[l];                     // t0 beta c / (p + 1)
+    }
 #pragma unroll
     for (int k = 0; k < kLsMaxPts; k++) {
-        if (k < m) {
-            const float v = fmaf(al[k], d, x);
-            const float w = pow_p1<PW>(v * inv, power);
-            two_sum_add(s[k], e[k], fmaf(bc, w, t0 * v));
+        if (k >= m) break;
+        float t[L];
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            const float v = fmaf(al[k], D[l], X[l]);
+            t[l] = fmaf(bc[l], pow_p1<PW>(v * inv[l], power), T[l] * v);
         }
+#pragma unroll
+        for (int st = 1; st < L; st <<= 1)
+#pragma unroll
+            for (int l = 0; l + st < L; l += 2 * st) t[l] += t[l + st];
+        kahan_add(s[k], e[k], t[0]);
     }
+}
+
+__device__ __forceinline__ void split4(const float4& v, float (&o)[8], int at) {
+    o[at] = v.x;
+    o[at + 1] = v.y;
+    o[at + 2] = v.z;
+    o[at + 3] = v.w;
 }
 
 template <bool VEC, int PW>
@@ -88,39 +110,40 @@ __global__ void __launch_bounds__(kPhiThreads, 2) k_phi(PhiArgs a) {
         const float4* d4 = reinterpret_cast<const float4*>(a.d);
         const float4* t4 = reinterpret_cast<const float4*>(a.t0);
         const float4* c4 = reinterpret_cast<const float4*>(a.c);
-        // two strides' loads in flight (128 bytes per thread) before the arithmetic
+        // two strides (8 links, 128 bytes per thread) in flight before the arithmetic
         int64_t i = tid;
         for (; i + stride < n4; i += 2 * stride) {
-            const float4 X = __ldcs(x4 + i), D = __ldcs(d4 + i), T = __ldcs(t4 + i), C = __ldcs(c4 + i);
-            const float4 X2 = __ldcs(x4 + i + stride), D2 = __ldcs(d4 + i + stride), T2 = __ldcs(t4 + i + stride),
-                         C2 = __ldcs(c4 + i + stride);
-            phi_link<PW>(X.x, D.x, T.x, C.x, kb, a.power, al, m, s, e);
-            phi_link<PW>(X.y, D.y, T.y, C.y, kb, a.power, al, m, s, e);
-            phi_link<PW>(X.z, D.z, T.z, C.z, kb, a.power, al, m, s, e);
-            phi_link<PW>(X.w, D.w, T.w, C.w, kb, a.power, al, m, s, e);
-            phi_link<PW>(X2.x, D2.x, T2.x, C2.x, kb, a.power, al, m, s, e);
-            phi_link<PW>(X2.y, D2.y, T2.y, C2.y, kb, a.power, al, m, s, e);
-            phi_link<PW>(X2.z, D2.z, T2.z, C2.z, kb, a.power, al, m, s, e);
-            phi_link<PW>(X2.w, D2.w, T2.w, C2.w, kb, a.power, al, m, s, e);
+            float X[8], D[8], T[8], C[8];
+            split4(__ldcs(x4 + i), X, 0);
+            split4(__ldcs(d4 + i), D, 0);
+            split4(__ldcs(t4 + i), T, 0);
+            split4(__ldcs(c4 + i), C, 0);
+            split4(__ldcs(x4 + i + stride), X, 4);
+            split4(__ldcs(d4 + i + stride), D, 4);
+            split4(__ldcs(t4 + i + stride), T, 4);
+            split4(__ldcs(c4 + i + stride), C, 4);
+            phi_group<PW, 8>(X, D, T, C, kb, a.power, al, m, s, e);
         }
         if (i < n4) {
             const float4 X = __ldcs(x4 + i), D = __ldcs(d4 + i), T = __ldcs(t4 + i), C = __ldcs(c4 + i);
-            phi_link<PW>(X.x, D.x, T.x, C.x, kb, a.power, al, m, s, e);
-            phi_link<PW>(X.y, D.y, T.y, C.y, kb, a.power, al, m, s, e);
-            phi_link<PW>(X.z, D.z, T.z, C.z, kb, a.power, al, m, s, e);
-            phi_link<PW>(X.w, D.w, T.w, C.w, kb, a.power, al, m, s, e);
+            const float Xa[4] = {X.x, X.y, X.z, X.w}, Da[4] = {D.x, D.y, D.z, D.w}, Ta[4] = {T.x, T.y, T.z, T.w},
+                        Ca[4] = {C.x, C.y, C.z, C.w};
+            phi_group<PW, 4>(Xa, Da, Ta, Ca, kb, a.power, al, m, s, e);
         }
         done = n4 * 4;
     }
-    for (int64_t i = done + tid; i < a.n; i += stride)
-        phi_link<PW>(__ldcs(a.x + i), __ldcs(a.d + i), __ldcs(a.t0 + i), __ldcs(a.c + i), kb, a.power, al, m, s, e);
+    for (int64_t i = done + tid; i < a.n; i += stride) {
+        const float X[1] = {__ldcs(a.x + i)}, D[1] = {__ldcs(a.d + i)}, T[1] = {__ldcs(a.t0 + i)},
+                    C[1] = {__ldcs(a.c + i)};
+        phi_group<PW, 1>(X, D, T, C, kb, a.power, al, m, s, e);
+    }
 
     // per point: thread pair -> float64, warp butterfly, warps in order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kLsMaxPts; k++) {
         if (k < m) {
-            double v = (double)s[k] + (double)e[k];
+            double v = (double)s[k] - (double)e[k];
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) s_w[warp][k] = v;
@@ -297,26 +320,15 @@ __global__ void k_ls_update(LsState* sp, double* result) {
 
 template <bool VEC>
 static const void* phi_fn(int power) {
-    switch (power) {
-        case 1: return reinterpret_cast<const void*>(&k_phi<VEC, 1>);
-        case 2: return reinterpret_cast<const void*>(&k_phi<VEC, 2>);
-        case 3: return reinterpret_cast<const void*>(&k_phi<VEC, 3>);
-        case 4: return reinterpret_cast<const void*>(&k_phi<VEC, 4>);
-        default: return reinterpret_cast<const void*>(&k_phi<VEC, 0>);
-    }
+    return power == 4 ? reinterpret_cast<const void*>(&k_phi<VEC, 4>) : reinterpret_cast<const void*>(&k_phi<VEC, 0>);
 }
 
 const void* phi_kernel(bool vec, int power) { return vec ? phi_fn<true>(power) : phi_fn<false>(power); }
 
 template <bool VEC>
 static void phi_go(const PhiArgs& a, int grid, cudaStream_t st) {
-    switch (a.power) {
-        case 1: k_phi<VEC, 1><<<grid, kPhiThreads, 0, st>>>(a); break;
-        case 2: k_phi<VEC, 2><<<grid, kPhiThreads, 0, st>>>(a); break;
-        case 3: k_phi<VEC, 3><<<grid, kPhiThreads, 0, st>>>(a); break;
-        case 4: k_phi<VEC, 4><<<grid, kPhiThreads, 0, st>>>(a); break;
-        default: k_phi<VEC, 0><<<grid, kPhiThreads, 0, st>>>(a); break;
-    }
+    if (a.power == 4) k_phi<VEC, 4><<<grid, kPhiThreads, 0, st>>>(a);
+    else k_phi<VEC, 0><<<grid, kPhiThreads, 0, st>>>(a);
 }
 
 cudaError_t launch_phi(const PhiArgs& a, int grid, bool vec, cudaStream_t st) {
