@@ -922,9 +922,13 @@ static pr_status run_phi(const float* x, const float* d, const float* t0, const 
     DevInfo di;
     pr_status s = device_info(&di, nullptr);
     if (s != PR_OK) return s;
+    // one grid for every point count (that of the up-to-8-point kernel), so
+    // that phi(alpha) has the same bits whatever else a pass evaluates
     int occ = 0;
-    if ((s = occupancy(phi_kernel(vec, power), kPhiThreads, &occ)) != PR_OK) return s;
-    if (occ < 1) return fail(PR_ERR_UNSUPPORTED, "evaluation kernel cannot run");
+    if ((s = occupancy(phi_kernel(vec, power, 8), kPhiThreads, &occ)) != PR_OK) return s;
+    int occ16 = 0;
+    if ((s = occupancy(phi_kernel(vec, power, kLsMaxPts), kPhiThreads, &occ16)) != PR_OK) return s;
+    if (occ < 1 || occ16 < 1) return fail(PR_ERR_UNSUPPORTED, "evaluation kernel cannot run");
     Workspace ws;
     if ((s = get_ws(st, &ws)) != PR_OK) return s;
     int64_t grid = (int64_t)di.sms * occ;

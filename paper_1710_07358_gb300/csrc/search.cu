@@ -54,10 +54,10 @@ __device__ __forceinline__ float pow_p1(float q, int power) {
 // L links of this thread at the first m points: per point the L terms are
 // summed pairwise in float32 and the sum enters the point's Kahan pair (the
 // loop over points stops at m, so a pass costs what its points need)
-template <int PW, int L>
+template <int PW, int L, int MP>
 __device__ __forceinline__ void phi_group(const float (&X)[L], const float (&D)[L], const float (&T)[L],
-                                          const float (&C)[L], float kb, int power, const float (&al)[kLsMaxPts],
-                                          int m, float (&s)[kLsMaxPts], float (&e)[kLsMaxPts]) {
+                                          const float (&C)[L], float kb, int power, const float (&al)[MP],
+                                          int m, float (&s)[MP], float (&e)[MP]) {
     float inv[L], bc[L];
 #pragma unroll
     for (int l = 0; l < L; l++) {
@@ -65,7 +65,7 @@ __device__ __forceinline__ void phi_group(const float (&X)[L], const float (&D)[
         bc[l] = T[l] * kb * C[l];                     // t0 beta c / (p + 1)
     }
 #pragma unroll
-    for (int k = 0; k < kLsMaxPts; k++) {
+    for (int k = 0; k < MP; k++) {
         if (k >= m) break;
         float t[L];
 #pragma unroll
@@ -88,14 +88,15 @@ __device__ __forceinline__ void split4(const float4& v, float (&o)[8], int at) {
     o[at + 3] = v.w;
 }
 
-template <bool VEC, int PW>
-__global__ void __launch_bounds__(kPhiThreads, 2) k_phi(PhiArgs a) {
+// MP: most points of a launch (8: three blocks per SM fit; 16: two)
+template <bool VEC, int PW, int MP>
+__global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 3 : 2) k_phi(PhiArgs a) {
     __shared__ double s_w[kPhiThreads / 32][kLsMaxPts];
     __shared__ bool s_last;
     const int m = a.m;
-    float al[kLsMaxPts], s[kLsMaxPts], e[kLsMaxPts];
+    float al[MP], s[MP], e[MP];
 #pragma unroll
-    for (int k = 0; k < kLsMaxPts; k++) {
+    for (int k = 0; k < MP; k++) {
         al[k] = k < m ? (float)a.pts[k] : 0.f;
         s[k] = 0.f;
         e[k] = 0.f;
@@ -122,26 +123,26 @@ __global__ void __launch_bounds__(kPhiThreads, 2) k_phi(PhiArgs a) {
             split4(__ldcs(d4 + i + stride), D, 4);
             split4(__ldcs(t4 + i + stride), T, 4);
             split4(__ldcs(c4 + i + stride), C, 4);
-            phi_group<PW, 8>(X, D, T, C, kb, a.power, al, m, s, e);
+            phi_group<PW, 8, MP>(X, D, T, C, kb, a.power, al, m, s, e);
         }
         if (i < n4) {
             const float4 X = __ldcs(x4 + i), D = __ldcs(d4 + i), T = __ldcs(t4 + i), C = __ldcs(c4 + i);
             const float Xa[4] = {X.x, X.y, X.z, X.w}, Da[4] = {D.x, D.y, D.z, D.w}, Ta[4] = {T.x, T.y, T.z, T.w},
                         Ca[4] = {C.x, C.y, C.z, C.w};
-            phi_group<PW, 4>(Xa, Da, Ta, Ca, kb, a.power, al, m, s, e);
+            phi_group<PW, 4, MP>(Xa, Da, Ta, Ca, kb, a.power, al, m, s, e);
         }
         done = n4 * 4;
     }
     for (int64_t i = done + tid; i < a.n; i += stride) {
         const float X[1] = {__ldcs(a.x + i)}, D[1] = {__ldcs(a.d + i)}, T[1] = {__ldcs(a.t0 + i)},
                     C[1] = {__ldcs(a.c + i)};
-        phi_group<PW, 1>(X, D, T, C, kb, a.power, al, m, s, e);
+        phi_group<PW, 1, MP>(X, D, T, C, kb, a.power, al, m, s, e);
     }
 
     // per point: thread pair -> float64, warp butterfly, warps in order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < kLsMaxPts; k++) {
+    for (int k = 0; k < MP; k++) {
         if (k < m) {
             double v = (double)s[k] - (double)e[k];
 #pragma unroll
@@ -318,22 +319,31 @@ __global__ void k_ls_update(LsState* sp, double* result) {
 
 // ---- launchers -------------------------------------------------------------
 
-template <bool VEC>
+template <bool VEC, int MP>
 static const void* phi_fn(int power) {
-    return power == 4 ? reinterpret_cast<const void*>(&k_phi<VEC, 4>) : reinterpret_cast<const void*>(&k_phi<VEC, 0>);
+    return power == 4 ? reinterpret_cast<const void*>(&k_phi<VEC, 4, MP>)
+                      : reinterpret_cast<const void*>(&k_phi<VEC, 0, MP>);
 }
 
-const void* phi_kernel(bool vec, int power) { return vec ? phi_fn<true>(power) : phi_fn<false>(power); }
+const void* phi_kernel(bool vec, int power, int m) {
+    if (m <= 8) return vec ? phi_fn<true, 8>(power) : phi_fn<false, 8>(power);
+    return vec ? phi_fn<true, kLsMaxPts>(power) : phi_fn<false, kLsMaxPts>(power);
+}
 
-template <bool VEC>
+template <bool VEC, int MP>
 static void phi_go(const PhiArgs& a, int grid, cudaStream_t st) {
-    if (a.power == 4) k_phi<VEC, 4><<<grid, kPhiThreads, 0, st>>>(a);
-    else k_phi<VEC, 0><<<grid, kPhiThreads, 0, st>>>(a);
+    if (a.power == 4) k_phi<VEC, 4, MP><<<grid, kPhiThreads, 0, st>>>(a);
+    else k_phi<VEC, 0, MP><<<grid, kPhiThreads, 0, st>>>(a);
 }
 
 cudaError_t launch_phi(const PhiArgs& a, int grid, bool vec, cudaStream_t st) {
-    if (vec) phi_go<true>(a, grid, st);
-    else phi_go<false>(a, grid, st);
+    if (a.m <= 8) {
+        if (vec) phi_go<true, 8>(a, grid, st);
+        else phi_go<false, 8>(a, grid, st);
+    } else {
+        if (vec) phi_go<true, kLsMaxPts>(a, grid, st);
+        else phi_go<false, kLsMaxPts>(a, grid, st);
+    }
     return cudaGetLastError();
 }
 

@@ -42,8 +42,8 @@ struct PhiArgs {
     unsigned* ticket;      // zero between launches
 };
 
-// The evaluation kernel for (vector path, power) and its launcher.
-const void* phi_kernel(bool vec, int power);
+// The evaluation kernel for (vector path, power, points) and its launcher.
+const void* phi_kernel(bool vec, int power, int m);
 cudaError_t launch_phi(const PhiArgs& a, int grid, bool vec, cudaStream_t st);
 cudaError_t launch_ls_init(LsState* s, double lo, double hi, int method, int count, int total, int depth,
                            cudaStream_t st);
