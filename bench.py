@@ -274,9 +274,9 @@ def linesearch(res, k, warmup, peak, st, g):
     """Golden-section (tolerance 1e-6 on [0, 1]: 29 iterations) and Fibonacci
     (31 evaluations) search of the Beckmann objective (BPR, beta 0.15, power
     4) over 2^24 synthetic links: four float32 arrays, 256 MiB per pass, more
-    than L2 holds.  depth D decides D iterations per pass over the links.
-    GB/s counts 16 bytes per link and pass; one evaluation pass alone is timed
-    with 2 and 6 points."""
+    than L2 holds.  One evaluation pass alone is timed first, with 2 and 6
+    points; then the searches, where depth D decides D iterations per pass
+    over the links.  GB/s counts 16 bytes per link and pass."""
     import torch
     from paper_1710_07358_gb300 import pr, synth
     dev = torch.device("cuda")
@@ -290,6 +290,14 @@ def linesearch(res, k, warmup, peak, st, g):
     d = y - x
     del y
     nb = 16 * n
+    for m in (2, 6):
+        al = torch.linspace(0.1, 0.9, m, dtype=torch.float64, device=dev)
+        ph = torch.empty(m, dtype=torch.float64, device=dev)
+        _, per = time_launches(lambda: pr.check(pr.pr_beckmann(x.data_ptr(), d.data_ptr(), t0.data_ptr(),
+                                                               c.data_ptr(), n, 0.15, 4, al.data_ptr(), m,
+                                                               ph.data_ptr(), st.cuda_stream)), k, warmup, st)
+        res["beckmann_pass_%dpts" % m] = {"us": round(per * 1e3, 2), "GB/s": round(gbs(nb, per), 1),
+                                          "frac": round(gbs(nb, per) / peak, 4)}
     out = torch.empty(4, dtype=torch.float64, device=dev)
     iters = pr.golden_iterations(0.0, 1.0, 1e-6)
     for method, count in (("golden", iters), ("fibonacci", 31)):
@@ -301,14 +309,6 @@ def linesearch(res, k, warmup, peak, st, g):
             res["linesearch_%s_d%d" % (method, depth)] = {
                 "us": round(per * 1e3, 1), "passes": passes, "GB/s": round(gbs(nb * passes, per), 1),
                 "frac": round(gbs(nb * passes, per) / peak, 4), "alpha": round(float(out[2].item()), 7)}
-    for m in (2, 6):
-        al = torch.linspace(0.1, 0.9, m, dtype=torch.float64, device=dev)
-        ph = torch.empty(m, dtype=torch.float64, device=dev)
-        _, per = time_launches(lambda: pr.check(pr.pr_beckmann(x.data_ptr(), d.data_ptr(), t0.data_ptr(),
-                                                               c.data_ptr(), n, 0.15, 4, al.data_ptr(), m,
-                                                               ph.data_ptr(), st.cuda_stream)), k, warmup, st)
-        res["beckmann_pass_%dpts" % m] = {"us": round(per * 1e3, 2), "GB/s": round(gbs(nb, per), 1),
-                                          "frac": round(gbs(nb, per) / peak, 4)}
     del x, d, t0, c
 
 
