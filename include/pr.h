@@ -262,7 +262,7 @@ pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream);
  * state lives on the device (a per-stream buffer made on first use, outside
  * graph capture): nothing is synchronised, and result (device, 4 doubles:
  * final a, b, the better of the last two points, its phi) is written by the
- * last kernel of the call. */
+ * last kernel of the call.  A search of P passes is P + 1 launches. */
 pr_status pr_beckmann(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
                       int32_t power, const double* alphas, int32_t m, double* out, pr_stream_t stream);
 pr_status pr_line_search(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,

@@ -916,7 +916,7 @@ static pr_status check_links(const float* x, const float* d, const float* t0, co
 // One evaluation pass: m points of pts, sums into out (all device memory).
 static pr_status run_phi(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
                          int32_t power, const double* pts, int m, double* out, double* partials, unsigned* ticket,
-                         cudaStream_t st) {
+                         cudaStream_t st, LsState* ls = nullptr, double* result = nullptr) {
     const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(d) |
                        reinterpret_cast<uintptr_t>(t0) | reinterpret_cast<uintptr_t>(cap)) % 16) == 0;
     DevInfo di;
@@ -935,7 +935,7 @@ static pr_status run_phi(const float* x, const float* d, const float* t0, const 
     const int64_t need = (n + 4LL * kPhiThreads - 1) / (4LL * kPhiThreads);
     if (grid > need) grid = need > 0 ? need : 1;
     if (grid > ws.gmax) grid = ws.gmax;
-    PhiArgs a{x, d, t0, cap, n, beta, power, pts, m, out, partials, ticket};
+    PhiArgs a{x, d, t0, cap, n, beta, power, pts, m, out, partials, ticket, ls, result};
     cudaError_t err = launch_phi(a, (int)grid, vec, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "evaluation launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -988,9 +988,9 @@ pr_status pr_line_search(const float* x, const float* d, const float* t0, const 
     for (bool first = true; first || iter < total; first = false) {
         const int lv = total - iter < depth ? total - iter : depth;
         const int m = (first ? 2 : 0) + (2 << lv) - 2;
-        if ((s = run_phi(x, d, t0, cap, n, beta, power, ls->pts, m, ls->vals, parts, ticket, st)) != PR_OK) return s;
-        err = launch_ls_update(ls, result, st);
-        if (err != cudaSuccess) return fail(PR_ERR_CUDA, "search update launch: %s", cudaGetErrorString(err));
+        if ((s = run_phi(x, d, t0, cap, n, beta, power, ls->pts, m, ls->vals, parts, ticket, st, ls, result)) !=
+            PR_OK)
+            return s;
         iter += lv;
     }
     return PR_OK;

@@ -13,12 +13,13 @@
 //            block order (the persistent reduction of Section 3 with a fixed
 //            combine order).  Error: within (p + 13) 2^-24 sum |term|.
 // k_ls_init  places the first two points and the speculative tree.
-// k_ls_update walks depth D decisions with the values of the pass, then places
-//            the next pass's tree: the 2^(D+1) - 2 points the next D
-//            iterations could need, so that D iterations cost one pass over
-//            the links instead of D, and the sequence of points is exactly
-//            the sequential search's.
-// Both small kernels run on one thread, with float64 operations written
+// ls_step    (one thread of a search pass's last block, after the sums) walks
+//            depth D decisions with the values of the pass, then places the
+//            next pass's tree: the 2^(D+1) - 2 points the next D iterations
+//            could need, so that D iterations cost one pass over the links
+//            instead of D, and the sequence of points is exactly the
+//            sequential search's.
+// k_ls_init and ls_step run on one thread, with float64 operations written
 // out (no contraction into FMA), so that the points match a float64
 // implementation that evaluates the same expressions in the same order.
 #include <cstdint>
@@ -28,6 +29,8 @@
 namespace pr {
 
 // ---- evaluation pass -------------------------------------------------------
+
+__device__ void ls_step(LsState& s, double* result);
 
 // Kahan's compensated add: c holds the negated low part lost so far, so the
 // running sum is s - c
@@ -172,6 +175,10 @@ __global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 3 : 2) k_phi(PhiArgs a)
         if (lane == 0) a.out[k] = v;
     }
     if (threadIdx.x == 0) *a.ticket = 0u;
+    if (a.ls) {
+        __syncthreads();                           // the sums of this pass are in a.out
+        if (threadIdx.x == 0) ls_step(*a.ls, a.result);
+    }
 }
 
 // ---- search state ----------------------------------------------------------
@@ -266,10 +273,10 @@ __global__ void k_ls_init(LsState* sp, double lo, double hi, int method, int cou
     s.npts = 2 + ls_tree(s, root, depth < total ? depth : total, 2);
 }
 
-// result: a, b, the better of the last two points and its value
-__global__ void k_ls_update(LsState* sp, double* result) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    LsState& s = *sp;
+// After a pass: walk its decisions, then place the next pass's points, or
+// finish and write result (a, b, the better of the last two points, its
+// value).  Run by one thread of the pass's last block.
+__device__ void ls_step(LsState& s, double* result) {
     if (s.done) return;
     const int base = s.first ? 2 : 0;
     if (s.first) {
@@ -353,9 +360,5 @@ cudaError_t launch_ls_init(LsState* s, double lo, double hi, int method, int cou
     return cudaGetLastError();
 }
 
-cudaError_t launch_ls_update(LsState* s, double* result, cudaStream_t st) {
-    k_ls_update<<<1, 32, 0, st>>>(s, result);
-    return cudaGetLastError();
-}
 
 }  // namespace pr

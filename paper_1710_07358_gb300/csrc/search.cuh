@@ -40,6 +40,8 @@ struct PhiArgs {
     double* out;           // m sums (device)
     double* partials;      // gridDim.x * kLsMaxPts block partials
     unsigned* ticket;      // zero between launches
+    LsState* ls;           // a search's state: its step runs after the sums (or null)
+    double* result;        // where the search's last step writes its result
 };
 
 // The evaluation kernel for (vector path, power, points) and its launcher.
@@ -47,6 +49,5 @@ const void* phi_kernel(bool vec, int power, int m);
 cudaError_t launch_phi(const PhiArgs& a, int grid, bool vec, cudaStream_t st);
 cudaError_t launch_ls_init(LsState* s, double lo, double hi, int method, int count, int total, int depth,
                            cudaStream_t st);
-cudaError_t launch_ls_update(LsState* s, double* result, cudaStream_t st);
 
 }  // namespace pr
