@@ -41,17 +41,12 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
     s = t;
 }
 
-// (v / c)^(p + 1) by repeated squaring for the usual power
+// (v / c)^(p + 1) for a power known only at run time
 template <int PW>
 __device__ __forceinline__ float pow_p1(float q, int power) {
-    if constexpr (PW == 4) {
-        const float q2 = q * q;
-        return (q2 * q2) * q;
-    } else {
-        float r = q;
-        for (int k = 0; k < power; k++) r *= q;
-        return r;
-    }
+    float r = q;
+    for (int k = 0; k < power; k++) r *= q;
+    return r;
 }
 
 // L links of this thread at the first m points: per point the L terms are
@@ -61,11 +56,18 @@ template <int PW, int L, int MP>
 __device__ __forceinline__ void phi_group(const float (&X)[L], const float (&D)[L], const float (&T)[L],
                                           const float (&C)[L], float kb, int power, const float (&al)[MP],
                                           int m, float (&s)[MP], float (&e)[MP]) {
+    // power 4: term = v (t0 + B v^4) with B = t0 beta / ((p + 1) c^4), five
+    // operations per point; other powers: t0 v + t0 beta c / (p + 1) (v / c)^(p + 1)
     float inv[L], bc[L];
 #pragma unroll
     for (int l = 0; l < L; l++) {
         inv[l] = __frcp_rn(C[l]);
-        bc[l] = T[l] * kb * C[l];                     // t0 beta c / (p + 1)
+        if constexpr (PW == 4) {
+            const float i2 = inv[l] * inv[l];
+            bc[l] = (T[l] * kb) * (i2 * i2);
+        } else {
+            bc[l] = T[l] * kb * C[l];
+        }
     }
 #pragma unroll
     for (int k = 0; k < MP; k++) {
@@ -74,7 +76,12 @@ __device__ __forceinline__ void phi_group(const float (&X)[L], const float (&D)[
 #pragma unroll
         for (int l = 0; l < L; l++) {
             const float v = fmaf(al[k], D[l], X[l]);
-            t[l] = fmaf(bc[l], pow_p1<PW>(v * inv[l], power), T[l] * v);
+            if constexpr (PW == 4) {
+                const float v2 = v * v;
+                t[l] = v * fmaf(bc[l], v2 * v2, T[l]);
+            } else {
+                t[l] = fmaf(bc[l], pow_p1<PW>(v * inv[l], power), T[l] * v);
+            }
         }
 #pragma unroll
         for (int st = 1; st < L; st <<= 1)
