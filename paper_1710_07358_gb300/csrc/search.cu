@@ -98,9 +98,9 @@ __device__ __forceinline__ void split4(const float4& v, float (&o)[8], int at) {
     o[at + 3] = v.w;
 }
 
-// MP: most points of a launch (8: three blocks per SM fit; 16: two)
+// MP: most points of a launch (8: two blocks per SM fit; 16: one)
 template <bool VEC, int PW, int MP>
-__global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 3 : 2) k_phi(PhiArgs a) {
+__global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 2 : 1) k_phi(PhiArgs a) {
     __shared__ double s_w[kPhiThreads / 32][kLsMaxPts];
     __shared__ bool s_last;
     const int m = a.m;
@@ -121,19 +121,39 @@ __global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 3 : 2) k_phi(PhiArgs a)
         const float4* d4 = reinterpret_cast<const float4*>(a.d);
         const float4* t4 = reinterpret_cast<const float4*>(a.t0);
         const float4* c4 = reinterpret_cast<const float4*>(a.c);
-        // two strides (8 links, 128 bytes per thread) in flight before the arithmetic
+        // groups of 8 links (two strides); the next group's loads are issued
+        // before the current group's arithmetic, so 256 bytes per thread stay
+        // in flight
+        auto load8 = [&](int64_t j, float (&X)[8], float (&D)[8], float (&T)[8], float (&C)[8]) {
+            split4(__ldcs(x4 + j), X, 0);
+            split4(__ldcs(d4 + j), D, 0);
+            split4(__ldcs(t4 + j), T, 0);
+            split4(__ldcs(c4 + j), C, 0);
+            split4(__ldcs(x4 + j + stride), X, 4);
+            split4(__ldcs(d4 + j + stride), D, 4);
+            split4(__ldcs(t4 + j + stride), T, 4);
+            split4(__ldcs(c4 + j + stride), C, 4);
+        };
         int64_t i = tid;
-        for (; i + stride < n4; i += 2 * stride) {
+        if (i + stride < n4) {
             float X[8], D[8], T[8], C[8];
-            split4(__ldcs(x4 + i), X, 0);
-            split4(__ldcs(d4 + i), D, 0);
-            split4(__ldcs(t4 + i), T, 0);
-            split4(__ldcs(c4 + i), C, 0);
-            split4(__ldcs(x4 + i + stride), X, 4);
-            split4(__ldcs(d4 + i + stride), D, 4);
-            split4(__ldcs(t4 + i + stride), T, 4);
-            split4(__ldcs(c4 + i + stride), C, 4);
-            phi_group<PW, 8, MP>(X, D, T, C, kb, a.power, al, m, s, e);
+            load8(i, X, D, T, C);
+            for (;;) {
+                const int64_t j = i + 2 * stride;
+                const bool more = j + stride < n4;
+                float Xn[8], Dn[8], Tn[8], Cn[8];
+                if (more) load8(j, Xn, Dn, Tn, Cn);
+                phi_group<PW, 8, MP>(X, D, T, C, kb, a.power, al, m, s, e);
+                i = j;
+                if (!more) break;
+#pragma unroll
+                for (int l = 0; l < 8; l++) {
+                    X[l] = Xn[l];
+                    D[l] = Dn[l];
+                    T[l] = Tn[l];
+                    C[l] = Cn[l];
+                }
+            }
         }
         if (i < n4) {
             const float4 X = __ldcs(x4 + i), D = __ldcs(d4 + i), T = __ldcs(t4 + i), C = __ldcs(c4 + i);
