@@ -483,6 +483,18 @@ def pinned_near_gpu(x_host, index):
     return t, sorted(cpus) if cpus else None
 
 
+def max_over_ranks(v: float, device="cpu") -> float:
+    """The largest of every rank's v (one all-reduce MAX; v itself when this
+    process is the only rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -561,9 +573,7 @@ def run_ours(args):
     total_ms, per_launch = time_launches(step, args.steps, 0, st)
     clocks = sampler.stop()
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
+        total_ms = max_over_ranks(total_ms, dev)
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
     value = gbs(nbytes * world, ms_per_step)
@@ -585,9 +595,7 @@ def run_ours(args):
             pr.reduce_host(pinned, "sum")
         e2e_s = time.perf_counter() - t
         if world > 1:
-            tt = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = tt.item()
+            e2e_s = max_over_ranks(e2e_s, dev)
         e2e_s /= ke
         e2e = {"value": round(gbs(nbytes * world, e2e_s * 1e3), 1), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": 4, "steps": ke,
