@@ -62,7 +62,8 @@ def golden_iterations(lo: float, hi: float, tol: float) -> int:
 
 
 def fibonacci(k: int) -> float:
-    """F_0 = F_1 = 1, F_k = F_{k-1} + F_{k-2}, as a float64."""
+    """F_0 = F_1 = 1, F_k = F_{k-1} + F_{k-2}, by float64 additions (exact up
+    to F_77, then IEEE-rounded)."""
     a, b = 1.0, 1.0
     for _ in range(k - 1):
         a, b = b, a + b

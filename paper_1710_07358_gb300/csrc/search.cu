@@ -210,7 +210,9 @@ __global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 2 : 1) k_phi(PhiArgs a)
 
 // ---- search state ----------------------------------------------------------
 
-// F_0 = F_1 = 1, F_k = F_{k-1} + F_{k-2} (exact in float64 up to F_78)
+// F_0 = F_1 = 1, F_k = F_{k-1} + F_{k-2} by float64 additions: exact up to
+// F_77; F_78 (above 2^53) is the IEEE rounding of the exact sum, as in any
+// float64 evaluation of the same recurrence
 __device__ double fib(int k) {
     double a = 1.0, b = 1.0;
     for (int i = 1; i < k; i++) {
