@@ -4,25 +4,26 @@
 // the reduction (Section 1.1), whose consumers the paper names (stream
 // compaction, counting and radix sort).
 //
-// k_scan  persistent blocks claim 32 KB tiles in order from an atomic
-// counter, so a block only ever waits for tiles that running blocks hold.
-// Tiles of an aligned input are staged in shared memory by bulk copies (a
-// ring of kScanStages per block), so a block has its next tiles in flight
-// while it works on one.  Per tile the block reduces the staged tile and
-// publishes its aggregate; warp 0 then looks back over the preceding tiles,
-// 32 at a time: tiles that already know their inclusive prefix end the walk,
-// the others contribute their aggregates (decoupled look-back).  The tile
-// publishes its inclusive prefix, and the block scans it a second time out of
-// shared memory, now with its prefix, and stores the outputs.  A block
-// reduces tile i + 1 before it looks back for tile i, so aggregates lead
-// look-backs by one tile.  The combiners are exact, associative and
-// commutative, so the result does not depend on how far a look-back walked
-// or in which order a tile's elements were combined.
+// k_scan  persistent blocks, one per SM, claim 32 KB tiles in order from an
+// atomic counter, so a block only ever waits for tiles that running blocks
+// hold.  Inside a block the warps have roles (see the kernel): a producer
+// thread stages claimed tiles of an aligned input in a ring of kScanStages
+// shared-memory buffers by bulk copies; reduce warps publish each tile's
+// aggregate as soon as its bytes land; look-back warps walk back over the
+// preceding tiles, 32 at a time: tiles that already know their inclusive
+// prefix end the walk, the others contribute their aggregates (decoupled
+// look-back), and the tile publishes its inclusive prefix; scan warps then
+// scan the tile out of shared memory with that prefix, store it, and free
+// the stage.  A tile's aggregate never waits for a look-back, so no
+// look-back waits behind another one.  The combiners are exact, associative
+// and commutative, so the result does not depend on how far a look-back
+// walked or in which order a tile's elements were combined.
 //
 // Status words carry an epoch (bumped by the last block of every launch), so
 // no reset pass runs between launches and graph replays see fresh flags.
 // Every wait is bounded: a wait that runs out sets kErrTimeout in the error
-// word (read by pr_last_device_error) and the block goes on with what it has.
+// word (read by pr_last_device_error) and the block winds down (every role
+// leaves its loop; the copies it started are waited for, bounded).
 #include <cstring>
 #include <type_traits>
 #include "kernels.cuh"
