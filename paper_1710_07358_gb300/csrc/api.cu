@@ -195,11 +195,13 @@ static std::map<CfgKey, pr_config> g_tuned;
 // at 1024 resident threads per SM streams at the HBM limit for the plain
 // reduction); pr_autotune / pr_tune_load refine them per (dtype, op, size).
 static pr_config default_cfg(int kind, int dtype, int op, int prec) {
-    (void)dtype; (void)op; (void)prec;
+    (void)prec;
     if (kind == PR_KIND_BACKWARD) return pr_config{512, 4, 4, 16};
     if (kind == PR_KIND_ROWS) return pr_config{512, 2, 2, 32};
     if (kind == PR_KIND_AXIS) return pr_config{256, 4, 2, 32};
-    if (kind == PR_KIND_SEGMENTED) return pr_config{256, 2, 4, 32};
+    // the split fp64 product keeps two accumulators' state per slot: two tiles in flight
+    if (kind == PR_KIND_SEGMENTED) return dtype == PR_F64 && op == PR_PROD ? pr_config{256, 2, 2, 32}
+                                                                          : pr_config{256, 2, 4, 32};
     return pr_config{512, 2, 2, 32};
 }
 
