@@ -41,6 +41,7 @@ sys.path.insert(0, ROOT)
 N_HEAD = 1 << 28
 METRIC = "reduce GB/s & % of HBM peak, n=2^28 fp32 sum; segmented/fwd+bwd vs plain"
 WORKLOAD = "plain fp32 sum, n=2^28 uniform[-1,1) (1 GiB), one scalar out"
+L2_NOTE = "input 1 GiB > 129 MB L2; no flush needed"
 KERNEL_SOURCES = ["common.cuh", "traits.cuh", "kernels.cuh", "inst_f32.cu"]
 
 
@@ -530,7 +531,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_HEAD, "op": "sum", "dtype": "f32",
-                                           "parallelism": "replicas"},
+                                           "parallelism": "replicas" if world > 1 else "single",
+                                           "l2": L2_NOTE},
             "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": "first %d elements of the n=2^28 workload per step" % m},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -616,7 +618,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N_HEAD, "op": "sum", "dtype": "f32",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "input 1 GiB > 129 MB L2; no flush needed", "launch": cfg},
+                       "l2": L2_NOTE, "launch": cfg},
             "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
             "result": res_val}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
