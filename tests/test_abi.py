@@ -207,3 +207,15 @@ def test_line_search_rejections():
     assert pr.pr_line_search(*ok, 0.0, 1.0, 0, 10, 4, F, None) == INVALID
     assert pr.pr_line_search(*ok, 0.0, 1.0, 0, 10, 2, None, None) == INVALID
     assert pr.pr_line_search(*ok, 0.0, 1.0, 0, 10, 2, F + 4, None) == INVALID
+
+
+def test_golden_iteration_count_matches_the_oracle():
+    """The binding's iteration count for a tolerance (host logic) is the
+    oracle's: the smallest K with (hi - lo) r^K <= tol."""
+    from oracle import linesearch as ols
+    for lo, hi in ((0.0, 1.0), (-3.0, 5.0), (0.25, 0.2500001)):
+        for tol in (1e-12, 1e-9, 1e-6, 1e-3, 0.5, 100.0):
+            k = pr.golden_iterations(lo, hi, tol)
+            assert k == ols.golden_iterations(lo, hi, tol)
+            assert (hi - lo) * ols.GOLDEN ** k <= tol * (1 + 1e-12)
+            assert k == 0 or (hi - lo) * ols.GOLDEN ** (k - 1) > tol
