@@ -32,6 +32,10 @@
  *     sequential loop).  Floating-point sums and products depend on the
  *     association order (Section 1.1, footnote on reordering); for a fixed
  *     configuration (pr_config) the order, and so the result, is fixed.
+ *   - F64 PROD keeps a separate integer exponent, so no partial product
+ *     overflows or underflows; half of each vector's factors multiply on the
+ *     fp64 pipe (rounded to nearest), half as 64-bit integer significands
+ *     (truncated, under 2^-61 each): within (n - 1) 2^-53 relative.
  *
  * Result types (pr_out_dtype):
  *   F32 -> F32;  F16/BF16: SUM,PROD -> F32, MAX,MIN -> same type;  F64 -> F64;
