@@ -241,8 +241,12 @@ pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream);
  * float32 each, device memory, 4-byte aligned (16-byte aligned: vector
  * loads).  beta >= 0, power in [1, 16].  Terms are evaluated in float32, a
  * thread's links summed pairwise per point into a Kahan (sum, compensation)
- * pair, then combined in float64 in a fixed order: deterministic, within
- * (power + 13) 2^-24 sum |term| of the exact sum of the terms.
+ * pair, then combined in float64 in a fixed order: deterministic.  Error,
+ * with u = 2^-24, counted from the operations (first order): each term's
+ * linear part t0 v within 3 u, its power part within c u (c = 20 for power
+ * 4, else 4 power + 7), the sums within 5 u of sum |term|; so phi is within
+ * u (8 sum |t0 v_i| + (c + 5) sum |power part_i|) <= (c + 5) u sum |term|
+ * of the exact sum of the exact terms at float32(alpha) and beta.
  *
  * pr_beckmann: out[k] = phi(alphas[k]) for k < m, m in [1, 16], in one pass
  * over the links (alphas and out: device, 8-byte aligned; alphas rounded to
@@ -269,6 +273,14 @@ pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream);
  * last kernel of the call.  A search of P passes is P + 1 launches. */
 pr_status pr_beckmann(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
                       int32_t power, const double* alphas, int32_t m, double* out, pr_stream_t stream);
+
+/* Golden-section iterations for a tolerance: *count = the smallest K >= 0
+ * with (hi - lo) r^K <= tol, r = (sqrt 5 - 1) / 2 (each iteration keeps r of
+ * the bracket), evaluated in double as (hi - lo) * pow(r, K).  Host only, no
+ * GPU needed.  lo < hi finite, tol > 0 finite; PR_ERR_INVALID otherwise or
+ * when K would exceed pr_line_search's limit of 200.  (Golden-section search,
+ * one of the reduction's consumers named in Section 1.) */
+pr_status pr_golden_iterations(double lo, double hi, double tol, int32_t* count);
 pr_status pr_line_search(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
                          int32_t power, double lo, double hi, pr_search method, int32_t count, int32_t depth,
                          double* result, pr_stream_t stream);
@@ -277,7 +289,12 @@ pr_status pr_line_search(const float* x, const float* d, const float* t0, const 
 /* Differentiation of a row reduction (F32 and F64)                         */
 /* ---------------------------------------------------------------------- */
 
-/* grad_in[r, c] = d out[r] / d x[r, c] * grad_out[r]  for a [rows, cols] x:
+/* The derivative of Section 1.1's reduction x_0 (x) ... (x) x_{n-1} with
+ * respect to each x_i, for the differentiable combiners (the paper gives no
+ * gradient: these are the combiners' own partial derivatives, with the
+ * derivative of MAX / MIN taken at the first arg-extremum and the product's
+ * prod_{j != i} x_j formed from the forward's zero count).
+ * grad_in[r, c] = d out[r] / d x[r, c] * grad_out[r]  for a [rows, cols] x:
  *   SUM:      grad_out[r]
  *   MAX/MIN:  grad_out[r] at c == argidx[r] (first arg-extremum), 0 elsewhere
  *   PROD:     zero_count 0: grad_out[r] * p_nz[r] / x[r,c];
@@ -290,7 +307,9 @@ pr_status pr_reduce_backward(pr_op op, pr_dtype dtype, const void* x, int64_t ro
                              const void* grad_out, const int64_t* argidx,
                              const pr_prod_aux* aux, void* grad_in, pr_stream_t stream);
 
-/* Gradient of pr_reduce_axis: grad_in[p, i, q] = d out[p, q] / d x[p, i, q] *
+/* Gradient of pr_reduce_axis (the partial derivatives above, for Section
+ * 1.1's reduction applied to every column of every [n, inner] slab):
+ * grad_in[p, i, q] = d out[p, q] / d x[p, i, q] *
  * grad_out[p, q], with the rules of pr_reduce_backward per output element
  * (argidx / aux as written by pr_reduce_axis).  grad_in: [outer, n, inner];
  * grad_out: [outer, inner]; x read only for PROD.  inner == 1 is
@@ -303,7 +322,10 @@ pr_status pr_reduce_axis_backward(pr_op op, pr_dtype dtype, const void* x, int64
 /* End to end from host memory                                              */
 /* ---------------------------------------------------------------------- */
 
-/* host_out[0] = reduction of host_x[0..n): the input is streamed to the device
+/* Section 1.1's reduction of a vector held in host memory, with the two
+ * stages of Section 2.3 split across chunks: stage 1 reduces each chunk on
+ * the device as it arrives, stage 2 combines the chunk partials.
+ * host_out[0] = reduction of host_x[0..n): the input is streamed to the device
  * in chunks (copies overlapped with the reduction of the previous chunk) and
  * the result copied back; returns after host_out is written.  host_x should be
  * pinned (cudaHostAlloc / cudaHostRegister) for full copy bandwidth.  Chunk
@@ -338,6 +360,30 @@ pr_status pr_reduce_host(const void* host_x, int64_t n, pr_dtype dtype, pr_op op
  *     tuned launch within the same error bounds. */
 pr_status pr_reduce_noalloc(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* out,
                             pr_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Failure handling: host-side fault injection (test hook)                   */
+/* ---------------------------------------------------------------------- */
+
+/* The paper has no counterpart: this is a hook for testing how failures
+ * propagate.  pr_debug_inject_fault arms a one-shot fault at `site`:
+ *   PR_FAULT_ALLOC   the library's next device allocation (per-stream
+ *                    workspace, axis partials, scan state, line-search state,
+ *                    host-pipeline buffers) fails: the entry point returns
+ *                    PR_ERR_NOMEM and keeps no partly made state, so a later
+ *                    call allocates afresh;
+ *   PR_FAULT_LAUNCH  the library's next kernel launch fails: the entry point
+ *                    returns PR_ERR_CUDA; launches it made before stay
+ *                    enqueued, nothing after is, and no completion ticket is
+ *                    left armed (kernels that never start touch none);
+ *   PR_FAULT_NONE    disarms.
+ * `after` (>= 0) allocations / launches of that site pass first.  The fault
+ * is taken on the host before the CUDA call, so no GPU is faulted; argument
+ * checks run first, so an invalid call neither fires nor consumes it.
+ * *pending (may be NULL) receives 1 if a fault was armed and had not fired.
+ * Process-wide; not meant to be armed while other threads use the library. */
+typedef enum { PR_FAULT_NONE = 0, PR_FAULT_ALLOC = 1, PR_FAULT_LAUNCH = 2 } pr_fault_site;
+pr_status pr_debug_inject_fault(int32_t site, int32_t after, int32_t* pending);
 
 /* ---------------------------------------------------------------------- */
 /* Set-up, status and tuning                                                */

@@ -48,6 +48,19 @@ def phi_terms(x, d, t0, c, beta: float, p: int, alpha: float) -> np.ndarray:
     return t0 * (v + float(beta) * c / (p + 1) * q ** (p + 1))
 
 
+def phi_parts(x, d, t0, c, beta: float, p: int, alpha: float):
+    """The two parts of every term, in float64: the linear part t0 v and the
+    power part t0 beta c / (p + 1) (v / c)^(p + 1).  Both have the sign of v,
+    so |term| = |linear| + |power|; an evaluation's error bound weighs the
+    two parts differently (the power part takes more roundings)."""
+    x = np.asarray(x, dtype=np.float32).astype(np.float64)
+    d = np.asarray(d, dtype=np.float32).astype(np.float64)
+    t0 = np.asarray(t0, dtype=np.float32).astype(np.float64)
+    c = np.asarray(c, dtype=np.float32).astype(np.float64)
+    v = x + float(alpha) * d
+    return t0 * v, t0 * float(beta) * c / (p + 1) * (v / c) ** (p + 1)
+
+
 def phi(x, d, t0, c, beta: float, p: int, alpha: float) -> float:
     """The objective at alpha: correctly rounded sum of the float64 terms."""
     return math.fsum(phi_terms(x, d, t0, c, beta, p, alpha).tolist())

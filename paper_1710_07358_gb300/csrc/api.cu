@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -77,6 +78,37 @@ pr_status fail(pr_status s, const char* fmt, ...) {
         cudaError_t e_ = (call);                                                            \
         if (e_ != cudaSuccess) return fail(PR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
+
+// ------------------------------------------------------------------------
+// Host-side fault injection (test hook, pr_debug_inject_fault)
+// ------------------------------------------------------------------------
+//
+// An armed fault makes the library's next device allocation (PR_FAULT_ALLOC)
+// or next kernel launch (PR_FAULT_LAUNCH), after `after` of them have passed,
+// fail as if the CUDA call had failed: the entry point returns the status it
+// returns for a real failure, with nothing further enqueued.  One-shot.  The
+// injection happens on the host, before the CUDA call, so no GPU is faulted.
+
+static std::atomic<int> g_fault_site{PR_FAULT_NONE};
+static std::mutex g_fault_mu;
+static int g_fault_after = 0;
+
+static bool inject(int site) {
+    if (g_fault_site.load(std::memory_order_relaxed) != site) return false;
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (g_fault_site.load(std::memory_order_relaxed) != site) return false;
+    if (g_fault_after > 0) {
+        g_fault_after--;
+        return false;
+    }
+    g_fault_site.store(PR_FAULT_NONE);
+    return true;
+}
+
+#define PR_INJECT_LAUNCH() \
+    do { if (inject(PR_FAULT_LAUNCH)) return fail(PR_ERR_CUDA, "kernel launch failed (injected by the test hook)"); } while (0)
+#define PR_INJECT_ALLOC() \
+    do { if (inject(PR_FAULT_ALLOC)) return fail(PR_ERR_NOMEM, "device allocation failed (injected by the test hook)"); } while (0)
 
 // ------------------------------------------------------------------------
 // Types
@@ -156,6 +188,7 @@ static pr_status get_ws(cudaStream_t st, Workspace* out) {
     const int gmax = di.sms * 32;
     const size_t bytes = ws_bytes(gmax);
     void* base = nullptr;
+    PR_INJECT_ALLOC();
     if (cudaMalloc(&base, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(PR_ERR_NOMEM, "workspace allocation of %zu bytes failed", bytes);
@@ -308,6 +341,7 @@ static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int pre
     int64_t head = (int64_t)(((uintptr_t)c.vec_bytes - addr % (uintptr_t)c.vec_bytes) % (uintptr_t)c.vec_bytes) / es;
     if (head > n) head = n;
     ReduceArgs a{x, n, head, out, part_out, out_f64 ? 1 : 0, ws, argidx};
+    PR_INJECT_LAUNCH();
     cudaError_t err = reinterpret_cast<ReduceLaunch>(e->launch)(a, grid, c.block, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "reduce launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -352,6 +386,7 @@ static pr_status run_segmented(const void* x, const int64_t* off, int64_t cols, 
     int cpb = 1, dyn = 0;
     seg_split(nseg, grid, ws.gmax, &cpb, &dyn);
     SegArgs a{x, off, cols, nseg, shift, out, argidx, paux, 0, cpb, dyn, ws};
+    PR_INJECT_LAUNCH();
     cudaError_t err = reinterpret_cast<SegLaunch>(e->launch)(a, grid, c.block, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "segmented launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -382,6 +417,7 @@ static pr_status run_rows(const void* x, int64_t rows, int64_t cols, int dtype, 
     const int64_t ntile = (rows * (cols / ve) + tile - 1) / tile;
     if (ntile < grid) grid = (int)ntile;
     RowArgs a{x, rows, cols, out, argidx, paux, 0, ws};
+    PR_INJECT_LAUNCH();
     cudaError_t err = reinterpret_cast<RowLaunch>(e->launch)(a, grid, c.block, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "row launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -413,6 +449,7 @@ static pr_status run_backward(int op, int dtype, const void* x, int64_t rows, in
     if (tiles < grid) grid = (int)tiles;
     const int64_t shift = (int64_t)(reinterpret_cast<uintptr_t>(gi) % (uintptr_t)c.vec_bytes) / es;
     BwdArgs a{x, g, argidx, aux, gi, rows, cols, shift, chunks, op};
+    PR_INJECT_LAUNCH();
     cudaError_t err = reinterpret_cast<BwdLaunch>(e->launch)(a, grid, c.block, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "backward launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -438,6 +475,7 @@ static pr_status axis_scratch(cudaStream_t st, size_t bytes, char** out) {
         w.axis = nullptr;
         w.axis_bytes = 0;
         size_t grow = bytes < ((size_t)1 << 20) ? ((size_t)1 << 20) : bytes;
+        PR_INJECT_ALLOC();
         if (cudaMalloc(&w.axis, grow) != cudaSuccess) {
             cudaGetLastError();
             return fail(PR_ERR_NOMEM, "axis partials: allocation of %zu bytes failed", grow);
@@ -465,6 +503,7 @@ static pr_status run_axis(const void* x, int64_t outer, int64_t n, int64_t inner
         if (!e) return fail(PR_ERR_UNSUPPORTED, "no axis kernel for dtype %d op %d precision %d", dtype, op, prec);
         const int64_t nout = outer * inner;
         int grid = (int)((nout + 255) / 256 < 4096 ? (nout + 255) / 256 : 4096);
+        PR_INJECT_LAUNCH();
         cudaError_t err = reinterpret_cast<AxisLaunch>(e->launch)(a, grid, 256, st);
         if (err != cudaSuccess) return fail(PR_ERR_CUDA, "axis launch: %s", cudaGetErrorString(err));
         return PR_OK;
@@ -508,6 +547,7 @@ static pr_status run_axis(const void* x, int64_t outer, int64_t n, int64_t inner
     const int wpb = c.block / 32;
     const int64_t grid = (warps + wpb - 1) / wpb;
     if (grid > 0x7fffffff) return fail(PR_ERR_INVALID, "axis reduction too large for one launch");
+    PR_INJECT_LAUNCH();
     cudaError_t err = reinterpret_cast<AxisLaunch>(e->launch)(a, (int)grid, c.block, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "axis launch: %s", cudaGetErrorString(err));
     if (a.splits > 1) {
@@ -517,6 +557,7 @@ static pr_status run_axis(const void* x, int64_t outer, int64_t n, int64_t inner
         const int64_t per_out = a.splits <= kAxisThreadFinish ? 1 : 32;   // threads per output
         const int64_t fgrid = (outer * inner * per_out + 255) / 256;
         if (fgrid > 0x7fffffff) return fail(PR_ERR_INVALID, "axis reduction too large for one launch");
+        PR_INJECT_LAUNCH();
         err = reinterpret_cast<AxisLaunch>(f->launch)(a, (int)fgrid, 256, st);
         if (err != cudaSuccess) return fail(PR_ERR_CUDA, "axis finish launch: %s", cudaGetErrorString(err));
     }
@@ -546,6 +587,7 @@ static pr_status scan_state(cudaStream_t st, int64_t tiles, ScanTile** recs, uns
         w.scan_tiles = 0;
         const int64_t grow = tiles < 4096 ? 4096 : tiles;
         const size_t bytes = (size_t)grow * sizeof(ScanTile) + 64;
+        PR_INJECT_ALLOC();
         if (cudaMalloc(&w.scan, bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(PR_ERR_NOMEM, "scan state: allocation of %zu bytes failed", bytes);
@@ -581,6 +623,7 @@ static pr_status search_state(cudaStream_t st, LsState** state, double** partial
             return fail(PR_ERR_INVALID, "line-search state: run a search on this stream once before graph capture");
         PR_CUDA(cudaStreamSynchronize(st));
         const size_t bytes = head + parts + 256;
+        PR_INJECT_ALLOC();
         if (cudaMalloc(&w.search, bytes) != cudaSuccess) {
             cudaGetLastError();
             w.search = nullptr;
@@ -619,6 +662,7 @@ static pr_status run_axis_backward(int op, int dtype, const void* x, int64_t out
     int64_t grid = (total + 255) / 256;
     const int64_t cap = (int64_t)di.sms * 64;
     if (grid > cap) grid = cap;
+    PR_INJECT_LAUNCH();
     cudaError_t err = reinterpret_cast<AxisBwdLaunch>(e->launch)(a, (int)grid, 256, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "axis backward launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -878,6 +922,7 @@ pr_status pr_scan(const void* x, int64_t n, pr_dtype dtype, pr_op op, int32_t ex
     int64_t grid = (int64_t)di.sms * occ;
     if (grid > tiles) grid = tiles;
     ScanArgs a{x, y, n, tiles, exclusive ? 1 : 0, recs, ctr, ws.err};
+    PR_INJECT_LAUNCH();
     cudaError_t err = reinterpret_cast<ScanLaunch>(e->launch)(a, (int)grid, kScanThreads, smem, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "scan launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -938,6 +983,7 @@ static pr_status run_phi(const float* x, const float* d, const float* t0, const 
     if (grid > need) grid = need > 0 ? need : 1;
     if (grid > ws.gmax) grid = ws.gmax;
     PhiArgs a{x, d, t0, cap, n, beta, power, pts, m, out, partials, ticket, ls, result};
+    PR_INJECT_LAUNCH();
     cudaError_t err = launch_phi(a, (int)grid, vec, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "evaluation launch: %s", cudaGetErrorString(err));
     return PR_OK;
@@ -961,6 +1007,21 @@ pr_status pr_beckmann(const float* x, const float* d, const float* t0, const flo
     return run_phi(x, d, t0, cap, n, beta, power, alphas, m, out, parts, ticket, st);
 }
 
+pr_status pr_golden_iterations(double lo, double hi, double tol, int32_t* count) {
+    g_msg.clear();
+    if (!count) return fail(PR_ERR_INVALID, "count is NULL");
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi)) return fail(PR_ERR_INVALID, "need finite lo < hi");
+    if (!std::isfinite(tol) || !(tol > 0.0)) return fail(PR_ERR_INVALID, "tol must be finite and > 0");
+    const double r = (std::sqrt(5.0) - 1.0) / 2.0;
+    const double w = hi - lo;
+    int k = 0;
+    while (w * std::pow(r, (double)k) > tol) {
+        if (++k > 200) return fail(PR_ERR_INVALID, "tolerance %g needs more than 200 iterations", tol);
+    }
+    *count = k;
+    return PR_OK;
+}
+
 pr_status pr_line_search(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
                          int32_t power, double lo, double hi, pr_search method, int32_t count, int32_t depth,
                          double* result, pr_stream_t stream) {
@@ -982,6 +1043,7 @@ pr_status pr_line_search(const float* x, const float* d, const float* t0, const 
     unsigned* ticket = nullptr;
     if ((s = search_state(st, &ls, &parts, &ticket)) != PR_OK) return s;
     const int total = method == PR_SEARCH_GOLDEN ? count : count - 2;
+    PR_INJECT_LAUNCH();
     cudaError_t err = launch_ls_init(ls, lo, hi, (int)method, count, total, depth, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "search init launch: %s", cudaGetErrorString(err));
     // passes: the first evaluates x1, x2 and the next min(depth, total)
@@ -995,6 +1057,17 @@ pr_status pr_line_search(const float* x, const float* d, const float* t0, const 
             return s;
         iter += lv;
     }
+    return PR_OK;
+}
+
+pr_status pr_debug_inject_fault(int32_t site, int32_t after, int32_t* pending) {
+    g_msg.clear();
+    if (site < PR_FAULT_NONE || site > PR_FAULT_LAUNCH) return fail(PR_ERR_INVALID, "unknown fault site %d", site);
+    if (after < 0) return fail(PR_ERR_INVALID, "after must be >= 0");
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (pending) *pending = g_fault_site.load() != PR_FAULT_NONE;
+    g_fault_after = after;
+    g_fault_site.store(site);
     return PR_OK;
 }
 
@@ -1066,45 +1139,86 @@ pr_status pr_reduce_host(const void* host_x, int64_t n, pr_dtype dtype, pr_op op
     PR_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_pipe_mu);
     HostPipe& hp = g_pipes[dev];
-    if (!hp.stage[0]) {
-        for (int b = 0; b < 2; b++) {
-            PR_CUDA(cudaMalloc(&hp.stage[b], kChunkBytes));
-            PR_CUDA(cudaEventCreateWithFlags(&hp.copied[b], cudaEventDisableTiming));
-            PR_CUDA(cudaEventCreateWithFlags(&hp.consumed[b], cudaEventDisableTiming));
+    if (!hp.copy) {
+        // staging buffers, events and the copy stream: kept only when all were made
+        HostPipe fresh;
+        auto release = [&fresh]() {
+            for (int b = 0; b < 2; b++) {
+                if (fresh.stage[b]) cudaFree(fresh.stage[b]);
+                if (fresh.copied[b]) cudaEventDestroy(fresh.copied[b]);
+                if (fresh.consumed[b]) cudaEventDestroy(fresh.consumed[b]);
+            }
+            if (fresh.dout) cudaFree(fresh.dout);
+            cudaGetLastError();
+        };
+        bool ok = true;
+        for (int b = 0; b < 2 && ok; b++) {
+            ok = !inject(PR_FAULT_ALLOC) && cudaMalloc(&fresh.stage[b], kChunkBytes) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&fresh.copied[b], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&fresh.consumed[b], cudaEventDisableTiming) == cudaSuccess;
         }
-        PR_CUDA(cudaMalloc(&hp.dout, 64));
-        PR_CUDA(cudaStreamCreateWithFlags(&hp.copy, cudaStreamNonBlocking));
+        ok = ok && !inject(PR_FAULT_ALLOC) && cudaMalloc(&fresh.dout, 64) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&fresh.copy, cudaStreamNonBlocking) == cudaSuccess;
+        if (!ok) {
+            release();
+            return fail(PR_ERR_NOMEM, "host pipeline: staging allocation failed");
+        }
+        hp = fresh;
     }
     const int es = elem_size(dtype);
     const int64_t chunk = (int64_t)(kChunkBytes / (size_t)es);
     const int64_t nchunks = n == 0 ? 1 : (n + chunk - 1) / chunk;
     if ((size_t)nchunks * kSlot > hp.parts_cap) {
+        PR_CUDA(cudaStreamSynchronize(st));
         if (hp.parts) PR_CUDA(cudaFree(hp.parts));
+        hp.parts = nullptr;
+        hp.parts_cap = 0;
+        PR_INJECT_ALLOC();
+        if (cudaMalloc(&hp.parts, (size_t)nchunks * kSlot) != cudaSuccess) {
+            cudaGetLastError();
+            hp.parts = nullptr;
+            return fail(PR_ERR_NOMEM, "host pipeline: chunk partials allocation failed");
+        }
         hp.parts_cap = (size_t)nchunks * kSlot;
-        PR_CUDA(cudaMalloc(&hp.parts, hp.parts_cap));
     }
     const pr_config c = lookup_cfg(PR_KIND_REDUCE, dtype, op, 0, chunk < n ? chunk : n);
-    // the copy stream starts after everything already queued on `st`
-    PR_CUDA(cudaEventRecord(hp.consumed[0], st));
-    PR_CUDA(cudaStreamWaitEvent(hp.copy, hp.consumed[0], 0));
-    PR_CUDA(cudaEventRecord(hp.consumed[1], st));
+    // The copy stream starts after everything already queued on `st`.  On a
+    // failure part-way, the copies already queued may still be reading
+    // host_x: wait for them (and for st) before returning, so that the caller
+    // may free or reuse host_x as soon as the call returns.
+    auto drain = [&](pr_status st_fail) {
+        cudaStreamSynchronize(hp.copy);
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        return st_fail;
+    };
+#define PR_HOST_CUDA(call)                                                                          \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return drain(fail(PR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_))); \
+    } while (0)
+    PR_HOST_CUDA(cudaEventRecord(hp.consumed[0], st));
+    PR_HOST_CUDA(cudaStreamWaitEvent(hp.copy, hp.consumed[0], 0));
+    PR_HOST_CUDA(cudaEventRecord(hp.consumed[1], st));
     for (int64_t k = 0; k < nchunks; k++) {
         const int b = (int)(k & 1);
         const int64_t lo = k * chunk;
         const int64_t len = n - lo < chunk ? n - lo : chunk;
-        PR_CUDA(cudaStreamWaitEvent(hp.copy, hp.consumed[b], 0));
+        PR_HOST_CUDA(cudaStreamWaitEvent(hp.copy, hp.consumed[b], 0));
         if (len > 0)
-            PR_CUDA(cudaMemcpyAsync(hp.stage[b], static_cast<const char*>(host_x) + lo * es, (size_t)len * es,
-                                    cudaMemcpyHostToDevice, hp.copy));
-        PR_CUDA(cudaEventRecord(hp.copied[b], hp.copy));
-        PR_CUDA(cudaStreamWaitEvent(st, hp.copied[b], 0));
+            PR_HOST_CUDA(cudaMemcpyAsync(hp.stage[b], static_cast<const char*>(host_x) + lo * es, (size_t)len * es,
+                                         cudaMemcpyHostToDevice, hp.copy));
+        PR_HOST_CUDA(cudaEventRecord(hp.copied[b], hp.copy));
+        PR_HOST_CUDA(cudaStreamWaitEvent(st, hp.copied[b], 0));
         s = run_reduce(hp.stage[b], len, dtype, op, 0, false, nullptr, hp.parts + k * kSlot, st, c);
-        if (s != PR_OK) return s;
-        PR_CUDA(cudaEventRecord(hp.consumed[b], st));
+        if (s != PR_OK) return drain(s);
+        PR_HOST_CUDA(cudaEventRecord(hp.consumed[b], st));
     }
+    if (inject(PR_FAULT_LAUNCH)) return drain(fail(PR_ERR_CUDA, "kernel launch failed (injected by the test hook)"));
     cudaError_t err = reinterpret_cast<CombineLaunch>(ce->launch)(hp.parts, (int)nchunks, hp.dout, 0, st);
-    if (err != cudaSuccess) return fail(PR_ERR_CUDA, "combine launch: %s", cudaGetErrorString(err));
-    PR_CUDA(cudaMemcpyAsync(host_out, hp.dout, (size_t)out_size(dtype, op), cudaMemcpyDeviceToHost, st));
+    if (err != cudaSuccess) return drain(fail(PR_ERR_CUDA, "combine launch: %s", cudaGetErrorString(err)));
+    PR_HOST_CUDA(cudaMemcpyAsync(host_out, hp.dout, (size_t)out_size(dtype, op), cudaMemcpyDeviceToHost, st));
+#undef PR_HOST_CUDA
     PR_CUDA(cudaStreamSynchronize(st));
     return PR_OK;
 }

@@ -11,7 +11,14 @@
 //            links per point summed pairwise and added to the point's Kahan
 //            pair, combined per block in float64 and by the last block in
 //            block order (the persistent reduction of Section 3 with a fixed
-//            combine order).  Error: within (p + 13) 2^-24 sum |term|.
+//            combine order).  Error (u = 2^-24, first order): the linear
+//            part t0 v of a term takes three roundings (the fma placing v,
+//            the fma or product adding t0, the final product); the power
+//            part twenty at power 4 (B: ten; v^4: four on v and three of its
+//            own; the fma and the product) and 4 p + 7 otherwise; the sums
+//            five (three pairwise levels, two for Kahan's update), the
+//            float64 combines below 2^-45.  So phi is within
+//            u (8 sum |t0 v| + (c_p + 5) sum |power part|).
 // k_ls_init  places the first two points and the speculative tree.
 // ls_step    (one thread of a search pass's last block, after the sums) walks
 //            depth D decisions with the values of the pass, then places the

@@ -59,12 +59,14 @@ _SIGS = {
     "pr_scan": [_P, _I64, _I, _I, ctypes.c_int32, _P, _P],
     "pr_check_bounded_wait": [ctypes.c_int32, _P],
     "pr_beckmann": [_P, _P, _P, _P, _I64, ctypes.c_float, _I32, _P, _I32, _P, _P],
+    "pr_golden_iterations": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_I32)],
     "pr_line_search": [_P, _P, _P, _P, _I64, ctypes.c_float, _I32, ctypes.c_double, ctypes.c_double, _I, _I32,
                        _I32, _P, _P],
     "pr_reduce_axis_backward": [_I, _I, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P],
     "pr_reduce_host": [_P, _I64, _I, _I, _P, _P],
     "pr_reduce_noalloc": [_P, _I64, _I, _I, _P, _P],
     "pr_prepare": [_P],
+    "pr_debug_inject_fault": [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_I32)],
     "pr_last_device_error": [_P, ctypes.POINTER(_I32)],
     "pr_get_config": [_I, _I, _I, _I, _I64, ctypes.POINTER(pr_config)],
     "pr_set_config": [_I, _I, _I, _I, _I64, ctypes.POINTER(pr_config)],
@@ -165,6 +167,10 @@ def pr_beckmann(x, d, t0, cap, n, beta, power, alphas, m, out, stream):
     return lib().pr_beckmann(x, d, t0, cap, n, beta, power, alphas, m, out, stream)
 
 
+def pr_golden_iterations(lo, hi, tol, count_ref):
+    return lib().pr_golden_iterations(lo, hi, tol, count_ref)
+
+
 def pr_line_search(x, d, t0, cap, n, beta, power, lo, hi, method, count, depth, result, stream):
     return lib().pr_line_search(x, d, t0, cap, n, beta, power, lo, hi, method, count, depth, result, stream)
 
@@ -179,6 +185,21 @@ def pr_reduce_noalloc(x, n, dtype, op, out, stream):
 
 def pr_prepare(stream):
     return lib().pr_prepare(stream)
+
+
+FAULT_SITES = {"none": 0, "alloc": 1, "launch": 2}
+
+
+def pr_debug_inject_fault(site, after, pending_ref):
+    return lib().pr_debug_inject_fault(site, after, pending_ref)
+
+
+def inject_fault(site: str, after: int = 0) -> bool:
+    """Arm (or, with "none", disarm) the library's one-shot host-side fault
+    hook; returns whether a fault was still pending before this call."""
+    p = ctypes.c_int32(0)
+    check(pr_debug_inject_fault(FAULT_SITES[site], after, ctypes.byref(p)))
+    return bool(p.value)
 
 
 def pr_last_device_error(stream, code_ref):
@@ -291,33 +312,48 @@ def reduce(x, op: str, precision: str = "plain", out_dtype: str | None = None, o
     return out
 
 
-def reduce_arg(x, op: str, stream=None):
+def reduce_arg(x, op: str, out=None, idx=None, stream=None):
     """(0-d value tensor, 0-d int64 index tensor): max or min of x and the index
-    of its first occurrence."""
+    of its first occurrence (written into out / idx when given)."""
     torch = _torch()
     if not x.is_cuda or not x.is_contiguous():
         raise ValueError("reduce_arg() needs a contiguous CUDA tensor")
     d = dtype_name(x)
-    out = torch.empty((), dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
-    idx = torch.empty((), dtype=torch.int64, device=x.device)
+    if out is None:
+        out = torch.empty((), dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
+    if idx is None:
+        idx = torch.empty((), dtype=torch.int64, device=x.device)
     check(pr_reduce_arg(_ptr(x), x.numel(), DTYPES[d], OPS[op], _ptr(out), _ptr(idx), _stream(x, stream)))
     return out, idx
 
 
+def _outputs(count, dtype_out, device, argidx, aux, out, argidx_out, aux_out):
+    """Output tensors of a reduction with `count` results: the caller's when
+    given, else new ones (argidx / aux only when requested)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(count, dtype=dtype_out, device=device)
+    ai = (argidx_out if argidx_out is not None else torch.empty(count, dtype=torch.int64, device=device)) \
+        if argidx else None
+    ax = (aux_out if aux_out is not None else torch.empty(count * 24, dtype=torch.int8, device=device)) \
+        if aux else None
+    return out, ai, ax
+
+
 def segmented_reduce(x, offsets, op: str, precision: str = "plain", argidx: bool = False,
-                     aux: bool = False, stream=None):
+                     aux: bool = False, stream=None, out=None, argidx_out=None, aux_out=None):
     """Per-segment reductions of x[offsets[s]:offsets[s+1]] (offsets: int64 CUDA tensor).
 
     Returns out, or (out, argidx) / (out, aux) when requested; aux is an
-    int8 tensor of nseg * 24 bytes (pr_prod_aux records), see prod_aux_fields()."""
+    int8 tensor of nseg * 24 bytes (pr_prod_aux records), see prod_aux_fields().
+    out / argidx_out / aux_out: caller-owned output tensors to write instead."""
     torch = _torch()
     d = dtype_name(x)
     nseg = offsets.numel() - 1
     if offsets.dtype != torch.int64 or not offsets.is_cuda or not offsets.is_contiguous():
         raise ValueError("offsets must be a contiguous int64 CUDA tensor")
-    out = torch.empty(max(nseg, 0), dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
-    ai = torch.empty(max(nseg, 0), dtype=torch.int64, device=x.device) if argidx else None
-    ax = torch.empty(max(nseg, 0) * 24, dtype=torch.int8, device=x.device) if aux else None
+    out, ai, ax = _outputs(max(nseg, 0), torch_dtype(out_dtype_name(d, op)), x.device, argidx, aux, out,
+                           argidx_out, aux_out)
     check(pr_segmented_reduce_aux(_ptr(x), _ptr(offsets), nseg, DTYPES[d], OPS[op], PRECISIONS[precision],
                                   _ptr(out), _ptr(ai), _ptr(ax), _stream(x, stream)))
     if argidx:
@@ -327,16 +363,16 @@ def segmented_reduce(x, offsets, op: str, precision: str = "plain", argidx: bool
     return out
 
 
-def reduce_rows(x, op: str, precision: str = "plain", argidx: bool = False, aux: bool = False, stream=None):
-    """Reduce a contiguous [rows, cols] CUDA tensor along its last dimension."""
-    torch = _torch()
+def reduce_rows(x, op: str, precision: str = "plain", argidx: bool = False, aux: bool = False, stream=None,
+                out=None, argidx_out=None, aux_out=None):
+    """Reduce a contiguous [rows, cols] CUDA tensor along its last dimension
+    (outputs as in segmented_reduce)."""
     if x.dim() != 2 or not x.is_contiguous():
         raise ValueError("reduce_rows needs a contiguous 2-D tensor")
     d = dtype_name(x)
     rows, cols = x.shape
-    out = torch.empty(rows, dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
-    ai = torch.empty(rows, dtype=torch.int64, device=x.device) if argidx else None
-    ax = torch.empty(rows * 24, dtype=torch.int8, device=x.device) if aux else None
+    out, ai, ax = _outputs(rows, torch_dtype(out_dtype_name(d, op)), x.device, argidx, aux, out, argidx_out,
+                           aux_out)
     check(pr_reduce_rows(_ptr(x), rows, cols, DTYPES[d], OPS[op], PRECISIONS[precision], _ptr(out), _ptr(ai),
                          _ptr(ax), _stream(x, stream)))
     if argidx:
@@ -359,7 +395,6 @@ def scan(x, op: str, exclusive: bool = False, out=None, stream=None):
 
 
 SEARCH = {"golden": 0, "fibonacci": 1}
-GOLDEN_RATIO_R = (5.0 ** 0.5 - 1.0) / 2.0
 
 
 def _links(x, d, t0, cap):
@@ -369,24 +404,25 @@ def _links(x, d, t0, cap):
             raise ValueError("x, d, t0, cap: contiguous float32 CUDA tensors of one length")
 
 
-def beckmann(x, d, t0, cap, alphas, beta: float = 0.15, power: int = 4, stream=None):
+def beckmann(x, d, t0, cap, alphas, beta: float = 0.15, power: int = 4, stream=None, out=None):
     """phi(alpha) of the Beckmann objective at each alpha (at most 16), one
-    pass over the links; a float64 CUDA tensor."""
+    pass over the links; a float64 CUDA tensor (out, when given)."""
     torch = _torch()
     _links(x, d, t0, cap)
     al = torch.as_tensor(alphas, dtype=torch.float64).reshape(-1).to(x.device)
-    out = torch.empty(al.numel(), dtype=torch.float64, device=x.device)
+    if out is None:
+        out = torch.empty(al.numel(), dtype=torch.float64, device=x.device)
     check(pr_beckmann(_ptr(x), _ptr(d), _ptr(t0), _ptr(cap), x.numel(), beta, power, _ptr(al), al.numel(),
                       _ptr(out), _stream(x, stream)))
     return out
 
 
 def golden_iterations(lo: float, hi: float, tol: float) -> int:
-    """Golden-section iterations until the bracket is at most tol wide."""
-    import math
-    if hi - lo <= tol:
-        return 0
-    return int(math.ceil(math.log(tol / (hi - lo)) / math.log(GOLDEN_RATIO_R) - 1e-12))
+    """Golden-section iterations until the bracket is at most tol wide
+    (pr_golden_iterations)."""
+    k = ctypes.c_int32(0)
+    check(pr_golden_iterations(lo, hi, tol, ctypes.byref(k)))
+    return k.value
 
 
 def line_search(x, d, t0, cap, lo: float = 0.0, hi: float = 1.0, beta: float = 0.15, power: int = 4,
@@ -421,20 +457,24 @@ def axis_shape(shape, dim):
 
 
 def reduce_axis(x, op: str, dim: int, precision: str = "plain", argidx: bool = False, aux: bool = False,
-                stream=None):
+                stream=None, out=None, argidx_out=None, aux_out=None):
     """Reduce a contiguous CUDA tensor along `dim` (the other dimensions kept).
 
     Returns out, or (out, argidx) / (out, aux) when requested, shaped like x
-    without `dim`; aux is an int8 tensor of 24-byte pr_prod_aux records."""
+    without `dim`; aux is an int8 tensor of 24-byte pr_prod_aux records.
+    out / argidx_out / aux_out: caller-owned output tensors to write instead."""
     torch = _torch()
     if not x.is_cuda or not x.is_contiguous():
         raise ValueError("reduce_axis needs a contiguous CUDA tensor")
     d = dtype_name(x)
     outer, n, inner = axis_shape(tuple(x.shape), dim)
     oshape = tuple(v for i, v in enumerate(x.shape) if i != dim % x.dim())
-    out = torch.empty(oshape, dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
-    ai = torch.empty(oshape, dtype=torch.int64, device=x.device) if argidx else None
-    ax = torch.empty(outer * inner * 24, dtype=torch.int8, device=x.device) if aux else None
+    if out is None:
+        out = torch.empty(oshape, dtype=torch_dtype(out_dtype_name(d, op)), device=x.device)
+    ai = (argidx_out if argidx_out is not None else torch.empty(oshape, dtype=torch.int64, device=x.device)) \
+        if argidx else None
+    ax = (aux_out if aux_out is not None else torch.empty(outer * inner * 24, dtype=torch.int8, device=x.device)) \
+        if aux else None
     check(pr_reduce_axis(_ptr(x), outer, n, inner, DTYPES[d], OPS[op], PRECISIONS[precision], _ptr(out), _ptr(ai),
                          _ptr(ax), _stream(x, stream)))
     if argidx:

@@ -76,3 +76,47 @@ def prod_rel_bound(n, dtype):
     place of the accumulation type (the worst case of any evaluation order)."""
     u = 2.0 ** -53 if dtype == "f64" else 2.0 ** -24
     return max(n - 1, 1) * u
+
+
+# ---------------------------------------------------------------------------
+# Canaries: device output buffers with guard bytes before and after them
+# ---------------------------------------------------------------------------
+
+GUARD = 256          # bytes on each side; keeps the buffer 256-byte aligned
+CANARY = 0xA5
+
+
+class Guarded:
+    """A device output tensor of `shape` / torch `dtype` inside a larger byte
+    buffer whose GUARD bytes before and after it hold CANARY.  check() fails
+    if a kernel wrote outside the tensor (the compute-sanitizer substitute
+    for writes past out, y, grad_in, argidx and aux)."""
+
+    def __init__(self, shape, dtype, device="cuda", fill=None):
+        import torch
+        shape = tuple(shape) if isinstance(shape, (tuple, list)) else (int(shape),)
+        numel = 1
+        for v in shape:
+            numel *= v
+        self.nbytes = numel * torch.empty((), dtype=dtype).element_size()
+        self.raw = torch.full((GUARD + self.nbytes + GUARD,), CANARY, dtype=torch.uint8, device=device)
+        self.tensor = self.raw[GUARD:GUARD + self.nbytes].view(dtype).view(shape)
+        if fill is not None:
+            self.tensor.fill_(fill)
+
+    def check(self):
+        import torch
+        torch.cuda.synchronize()
+        head = self.raw[:GUARD]
+        tail = self.raw[GUARD + self.nbytes:]
+        assert bool(torch.all(head == CANARY)), "write before the output buffer"
+        assert bool(torch.all(tail == CANARY)), "write past the end of the output buffer"
+        return self.tensor
+
+
+def guarded_like(shape, name):
+    """Guarded output for one of the library's dtype names (f32, i64, ...)."""
+    from paper_1710_07358_gb300 import pr
+    import torch
+    dt = pr.torch_dtype(name) if name != "aux" else torch.int8
+    return Guarded(shape, dt)

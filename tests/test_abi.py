@@ -209,13 +209,39 @@ def test_line_search_rejections():
     assert pr.pr_line_search(*ok, 0.0, 1.0, 0, 10, 2, F + 4, None) == INVALID
 
 
-def test_golden_iteration_count_matches_the_oracle():
-    """The binding's iteration count for a tolerance (host logic) is the
-    oracle's: the smallest K with (hi - lo) r^K <= tol."""
-    from oracle import linesearch as ols
-    for lo, hi in ((0.0, 1.0), (-3.0, 5.0), (0.25, 0.2500001)):
-        for tol in (1e-12, 1e-9, 1e-6, 1e-3, 0.5, 100.0):
+def test_golden_iteration_count_closed_form(L):
+    """pr_golden_iterations returns the smallest K with (hi - lo) r^K <= tol,
+    r = (sqrt 5 - 1) / 2: the bracket after K iterations is within tol and
+    the one after K - 1 is not."""
+    import math
+    r = (math.sqrt(5.0) - 1.0) / 2.0
+    for lo, hi in ((0.0, 1.0), (-3.0, 5.0), (0.25, 0.2500001), (10.0, 1e6)):
+        for tol in (1e-12, 1e-9, 1e-6, 1e-3, 0.5, 100.0, 1e7):
             k = pr.golden_iterations(lo, hi, tol)
-            assert k == ols.golden_iterations(lo, hi, tol)
-            assert (hi - lo) * ols.GOLDEN ** k <= tol * (1 + 1e-12)
-            assert k == 0 or (hi - lo) * ols.GOLDEN ** (k - 1) > tol
+            assert (hi - lo) * r ** k <= tol
+            assert k == 0 or (hi - lo) * r ** (k - 1) > tol
+    assert pr.golden_iterations(0.0, 1.0, 1e-6) == 29            # the benchmark's search: r^29 = 8.7e-7
+    k = ctypes.c_int32(-1)
+    for bad in ((1.0, 1.0, 1e-3), (0.0, 1.0, 0.0), (0.0, 1.0, -1.0), (0.0, float("inf"), 1e-3),
+                (0.0, 1.0, float("nan")), (0.0, 1.0, 1e-300)):
+        assert pr.pr_golden_iterations(*bad, ctypes.byref(k)) == INVALID
+    assert pr.pr_golden_iterations(0.0, 1.0, 1e-3, None) == INVALID
+
+
+def test_fault_hook_arguments_and_validation_order(L):
+    """The host-side fault hook: bad arguments are refused; argument checks run
+    before it, so rejected calls neither fire nor consume an armed fault."""
+    pending = ctypes.c_int32(7)
+    assert pr.pr_debug_inject_fault(3, 0, ctypes.byref(pending)) == INVALID
+    assert pr.pr_debug_inject_fault(-1, 0, None) == INVALID
+    assert pr.pr_debug_inject_fault(1, -1, None) == INVALID
+    assert pr.inject_fault("none") is False
+    for site in ("launch", "alloc"):
+        assert pr.inject_fault(site, after=2) is False
+        assert pr.pr_reduce(FAKE, -1, F32, SUM, FAKE, None) == INVALID
+        assert pr.pr_segmented_reduce(FAKE, None, 4, F32, SUM, FAKE, None) == INVALID
+        assert pr.pr_scan(None, 4, I32, SUM, 0, FAKE, None) == INVALID
+        assert pr.pr_reduce_backward(MAX, F32, None, 4, 4, FAKE, None, None, FAKE, None) == INVALID
+        assert pr.pr_line_search(FAKE, FAKE, FAKE, FAKE, 100, 0.15, 4, 1.0, 1.0, 0, 10, 2, FAKE, None) == INVALID
+        assert pr.inject_fault("none") is True            # still armed: nothing consumed it
+        assert pr.inject_fault("none") is False

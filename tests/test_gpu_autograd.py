@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_1710_07358_gb300 import pr, synth
 from paper_1710_07358_gb300.autograd import reduce as ad_reduce
-from gpu_helpers import to_device
+from gpu_helpers import to_device, Guarded
 
 pytestmark = pytest.mark.gpu
 
@@ -85,11 +85,13 @@ def test_backward_unaligned_rows():
     t = to_device(x.reshape(-1), "f32", 1).view(rows, cols)
     g = torch.arange(1, rows + 1, dtype=torch.float32, device="cuda")
     for op in ("sum", "max"):
+        gd = Guarded((rows, cols), torch.float32)
         if op == "max":
             _, ai = pr.reduce_rows(t, "max", argidx=True)
-            gi = pr.reduce_backward("max", t, g, argidx=ai)
+            gi = pr.reduce_backward("max", t, g, argidx=ai, out=gd.tensor)
         else:
-            gi = pr.reduce_backward("sum", t, g)
+            gi = pr.reduce_backward("sum", t, g, out=gd.tensor)
+        gd.check()
         want = oracle.grad(x, "f32", op, g.cpu().numpy())
         assert np.array_equal(gi.double().cpu().numpy(), want)
 

@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_1710_07358_gb300 import pr, synth
 from paper_1710_07358_gb300.autograd import reduce as ad_reduce
-from gpu_helpers import to_device, values_of, same_float, sum_bound, prod_rel_bound
+from gpu_helpers import to_device, values_of, same_float, sum_bound, prod_rel_bound, guarded_like
 
 pytestmark = pytest.mark.gpu
 
@@ -53,9 +53,13 @@ def check_axis(x, dtype, op, shape, got, argidx=None, precision="plain"):
 
 
 def run_axis(x, dtype, op, shape, offset=0, argidx=False, precision="plain"):
+    """Outputs of the middle-axis reduction, written into canary-guarded buffers."""
     t = to_device(x, dtype, offset).view(*shape)
-    res = pr.reduce_axis(t, op, 1, precision=precision, argidx=argidx)
     od = pr.out_dtype_name(dtype, op)
+    oshape = (shape[0], shape[2])
+    go, ga = guarded_like(oshape, od), guarded_like(oshape, "i64")
+    res = pr.reduce_axis(t, op, 1, precision=precision, argidx=argidx, out=go.tensor, argidx_out=ga.tensor)
+    go.check(), ga.check()
     if argidx:
         return values_of(res[0], od), res[1].reshape(-1).cpu().numpy()
     return values_of(res, od), None

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_1710_07358_gb300 import pr, synth
-from gpu_helpers import to_device, values_of, same_float, sum_bound, prod_rel_bound
+from gpu_helpers import to_device, values_of, same_float, sum_bound, prod_rel_bound, guarded_like
 
 pytestmark = pytest.mark.gpu
 
@@ -57,10 +57,12 @@ def check(x, dtype, op, got, precision="plain"):
 
 
 def run(x, dtype, op, offset=0, precision="plain", out_dtype=None):
+    """The reduction of x, written into a canary-guarded output."""
     t = to_device(x, dtype, offset)
-    out = pr.reduce(t, op, precision=precision, out_dtype=out_dtype)
     od = out_dtype or pr.out_dtype_name(dtype, op)
-    return values_of(out, od)[0]
+    g = guarded_like((), od)
+    pr.reduce(t, op, precision=precision, out_dtype=out_dtype, out=g.tensor)
+    return values_of(g.check(), od)[0]
 
 
 @pytest.mark.parametrize("dtype,op", PAIRS)
@@ -269,7 +271,9 @@ def test_reduce_arg_first_index(dtype, op):
             x = np.array(x, copy=True)
             x.reshape(-1)[n // 3] = x.reshape(-1)[oracle.argext(x, dtype, op)[1]]
         t = to_device(x, dtype, offset)
-        val, idx = pr.reduce_arg(t, op)
+        gv, gi = guarded_like((), pr.out_dtype_name(dtype, op)), guarded_like((), "i64")
+        val, idx = pr.reduce_arg(t, op, out=gv.tensor, idx=gi.tensor)
+        gv.check(), gi.check()
         wv, wi = oracle.argext(x, dtype, op)
         got = values_of(val, pr.out_dtype_name(dtype, op))[0]
         assert int(idx.item()) == wi, (n, int(idx.item()), wi)

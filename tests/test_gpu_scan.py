@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 from paper_1710_07358_gb300 import pr, synth
-from gpu_helpers import to_device, bits_of
+from gpu_helpers import to_device, bits_of, guarded_like
 
 pytestmark = pytest.mark.gpu
 
@@ -50,8 +50,11 @@ def assert_same(got, want, dtype):
 
 
 def run(x, dtype, op, exclusive, offset=0):
+    """The scan of x, written into a canary-guarded output."""
     t = to_device(x, dtype, offset)
-    y = pr.scan(t, op, exclusive=exclusive)
+    g = guarded_like(t.numel(), pr.out_dtype_name(dtype, op))
+    y = pr.scan(t, op, exclusive=exclusive, out=g.tensor)
+    g.check()
     return got_values(y, dtype, op)
 
 

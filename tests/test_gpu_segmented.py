@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_1710_07358_gb300 import pr, synth
-from gpu_helpers import to_device, values_of, same_float, sum_bound, prod_rel_bound
+from gpu_helpers import to_device, values_of, same_float, sum_bound, prod_rel_bound, guarded_like
 
 pytestmark = pytest.mark.gpu
 
@@ -41,9 +41,15 @@ def check_segments(x, off, dtype, op, out_vals, argidx=None, precision="plain"):
 
 
 def run_seg(x, off, dtype, op, offset=0, argidx=False, aux=False, precision="plain"):
+    """Segment results (and argidx / aux), written into canary-guarded outputs."""
     t = to_device(x, dtype, offset)
-    res = pr.segmented_reduce(t, dev_off(off), op, precision=precision, argidx=argidx, aux=aux)
+    nseg = len(off) - 1
     od = pr.out_dtype_name(dtype, op)
+    go, ga, gx = guarded_like(nseg, od), guarded_like(nseg, "i64"), guarded_like(nseg * 24, "aux")
+    res = pr.segmented_reduce(t, dev_off(off), op, precision=precision, argidx=argidx, aux=aux, out=go.tensor,
+                              argidx_out=ga.tensor, aux_out=gx.tensor)
+    for g in (go, ga, gx):
+        g.check()
     if argidx:
         return values_of(res[0], od), res[1].cpu().numpy()
     if aux:
@@ -239,16 +245,19 @@ def test_row_kernel_shapes(rows, cols, offset):
     t = to_device(x, "f32", offset).view(rows, cols)
     off = np.arange(rows + 1, dtype=np.int64) * cols
     for op in ("sum", "max", "min"):
+        go, ga = guarded_like(rows, "f32"), guarded_like(rows, "i64")
         if op == "sum":
-            out = pr.reduce_rows(t, op)
-            check_segments(x, off, "f32", op, values_of(out, "f32"))
+            out = pr.reduce_rows(t, op, out=go.tensor)
+            check_segments(x, off, "f32", op, values_of(go.check(), "f32"))
         else:
-            out, ai = pr.reduce_rows(t, op, argidx=True)
-            check_segments(x, off, "f32", op, values_of(out, "f32"), argidx=ai.cpu().numpy())
+            out, ai = pr.reduce_rows(t, op, argidx=True, out=go.tensor, argidx_out=ga.tensor)
+            check_segments(x, off, "f32", op, values_of(go.check(), "f32"), argidx=ga.check().cpu().numpy())
     xp = synth.uniform_f32(rows * cols, 7, 1 - 2.0 ** -7, 1 + 2.0 ** -7)
     xp[::997] = 0.0
     tp = to_device(xp, "f32", offset).view(rows, cols)
-    out, ax = pr.reduce_rows(tp, "prod", aux=True)
+    go, gx = guarded_like(rows, "f32"), guarded_like(rows * 24, "aux")
+    out, ax = pr.reduce_rows(tp, "prod", aux=True, out=go.tensor, aux_out=gx.tensor)
+    go.check(), gx.check()
     p_nz, zc, zi = (v.cpu().numpy() for v in pr.prod_aux_fields(ax))
     vals = values_of(out, "f32")
     for r in list(range(min(rows, 20))) + [rows - 1]:

@@ -116,3 +116,25 @@ def test_searches_agree_with_dense_grid(p):
         a_star = ls.quadratic_minimizer(x, d, t0, c, beta)
         assert a - 1e-9 <= a_star <= b + 1e-9
         assert abs(a_star - grid[k]) <= step
+
+
+@pytest.mark.parametrize("p", [1, 4, 6])
+def test_phi_parts_split_each_term(p):
+    """The linear and power parts add up to the term (sharing its sign when
+    p + 1 is odd, or where v >= 0), and their derivatives along d are the
+    free-flow cost sum t0 d and the congestion cost sum t0 beta (v / c)^p d."""
+    x, d, t0, c = network(3000, 5)
+    for alpha in (0.0, 0.4, 2.5):
+        lin, pw = ls.phi_parts(x, d, t0, c, 0.15, p, alpha)
+        t = ls.phi_terms(x, d, t0, c, 0.15, p, alpha)
+        assert np.allclose(lin + pw, t, rtol=1e-15, atol=0)
+        same = (lin >= 0) if p % 2 else np.ones_like(lin, dtype=bool)
+        assert np.all((np.abs(lin) + np.abs(pw))[same] <= np.abs(t)[same] * (1 + 1e-15))
+    h, a0 = 1e-4, 0.3
+    part = lambda a, k: math.fsum(ls.phi_parts(x, d, t0, c, 0.15, p, a)[k].tolist())
+    x64, d64, t64, c64 = (np.asarray(v, dtype=np.float64) for v in (x, d, t0, c))
+    v = x64 + a0 * d64
+    want_lin = math.fsum((t64 * d64).tolist())
+    want_pw = math.fsum((t64 * 0.15 * (v / c64) ** p * d64).tolist())
+    assert (part(a0 + h, 0) - part(a0 - h, 0)) / (2 * h) == pytest.approx(want_lin, rel=1e-7)
+    assert (part(a0 + h, 1) - part(a0 - h, 1)) / (2 * h) == pytest.approx(want_pw, rel=1e-6)
