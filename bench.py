@@ -9,14 +9,19 @@ Also reported in the same line:
   e2e          the same metric through pr_reduce_host (pinned host buffer, chunked
                host->device copies, result read back) per step;
   roofline     achieved / measured HBM peak of the dominant kernel, per launch;
-  cpu_baseline the CPU oracle (exact fixed-point sum, one host core) on the same data;
+  cpu_baseline the CPU oracle (exact fixed-point sum, one host core) on the same data,
+               and beside it the chunked multi-core loop over every core the process
+               may use (cpu_baseline_multicore), both with the CPU model;
   forms        every op / dtype of the sweep at 2^28, the precision modes, the
                segmented form (4096 log-uniform segments, autotuned, replayed from a
                CUDA graph), forward+backward of [64, 2^20] row reductions, and
                reductions of a non-last axis (1 GiB: middle axis of [16, 4096,
                4096] with its gradient, first axis of [16384, 16384]), one-pass
-               prefix scans of 2^28 elements, and golden-section / Fibonacci line
-               searches of the Beckmann objective over 2^24 links.
+               prefix scans of 2^28 elements, golden-section / Fibonacci line
+               searches of the Beckmann objective over 2^24 links, and the n sweep
+               of the fp32 sum (2^10 .. 2^30 and the paper's 5 533 214);
+               each form's results are checked against the oracle ("check":
+               errors against their bounds, or exactness) in the CPU-baseline leg.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms]
 
@@ -166,14 +171,128 @@ def cpu_oracle_sum(x):
     return time.perf_counter() - t
 
 
+def cpu_model():
+    """The host CPU's model name as lscpu reports it (else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_chunked_baseline(x, reps=5):
+    """The multi-core CPU baseline: Algorithm 1 with a double accumulator per
+    contiguous chunk, one chunk per core this process may run on, chunk sums
+    added in order.  Returns (GB/s, cores)."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    oracle.sum_f64_chunked(x, "f32", cores)
+    best = None
+    for _ in range(reps):
+        t = time.perf_counter()
+        oracle.sum_f64_chunked(x, "f32", cores)
+        dt = time.perf_counter() - t
+        best = dt if best is None or dt < best else best
+    return gbs(x.size * 4, best * 1e3), cores
+
+
+class Checker:
+    """The oracle leg's checks of every form's results (run after the form's
+    timed region, on host copies of its inputs): exact results are compared
+    bit for bit, float sums by their exact error against the bounds of
+    include/pr.h, products by relative error.  Independent oracle calls run
+    on a thread pool (the oracle's C loops release the GIL)."""
+
+    def __init__(self):
+        import concurrent.futures
+        import oracle
+        self.oracle = oracle
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=max(1, len(os.sched_getaffinity(0))))
+
+    @staticmethod
+    def host(t):
+        """numpy copy of a CUDA tensor in the oracle's storage type."""
+        import numpy as np
+        import torch
+        if t.dtype in (torch.bfloat16, torch.float16):
+            a = t.view(torch.int16).cpu().numpy().view(np.uint16)
+            return a.view(np.float16) if t.dtype == torch.float16 else a
+        if hasattr(torch, "uint32") and t.dtype == torch.uint32:
+            return t.view(torch.int32).cpu().numpy().view(np.uint32)
+        return t.cpu().numpy()
+
+    @staticmethod
+    def value(t):
+        """Python value of a 0-d CUDA result tensor."""
+        import torch
+        if hasattr(torch, "uint32") and t.dtype == torch.uint32:
+            return int(t.view(torch.int32).item()) & 0xFFFFFFFF
+        if t.dtype in (torch.bfloat16, torch.float16):
+            return float(t.float().item())
+        return t.item()
+
+    def sum(self, x, dtype, got, precision="plain"):
+        o = self.oracle
+        fa = self.pool.submit(o.abs_sum, x, dtype)
+        fe = self.pool.submit(o.sum_error, x, dtype, float(got))
+        a, err = fa.result(), fe.result()
+        bound = 2.0 ** -24 * a if precision == "compensated" else 1e-6 * a
+        return {"abs_err": err, "bound": bound, "rel_to_sum_abs": err / a if a else 0.0, "ok": err <= bound}
+
+    def exact(self, x, dtype, op, got):
+        want = self.oracle.reduce(x, dtype, op)
+        ok = (got == want) if not isinstance(want, float) else (got == want or (got != got and want != want))
+        return {"exact": bool(ok)}
+
+    def prod(self, x, dtype, got):
+        want = self.oracle.reduce(x, dtype, "prod")
+        rel = abs(got - want) / abs(want) if want else abs(got)
+        bound = max(x.size - 1, 1) * (2.0 ** -53 if dtype == "f64" else 2.0 ** -24)
+        return {"rel_err": rel, "bound": bound, "ok": rel <= bound}
+
+    def segments(self, x, off, op, got):
+        """Every segment: sums by exact error, max by equality."""
+        o = self.oracle
+        nseg = len(off) - 1
+
+        def one(k):
+            seg = x[off[k]:off[k + 1]]
+            if op == "sum":
+                a = o.abs_sum(seg, "f32")
+                e = o.sum_error(seg, "f32", float(got[k]))
+                return e, 1e-6 * a
+            v = o.reduce(seg, "f32", op)
+            return (0.0 if v == float(got[k]) else float("inf")), 0.0
+        errs = list(self.pool.map(one, range(nseg)))
+        worst = max(e / b if b else (0.0 if e == 0 else float("inf")) for e, b in errs)
+        return {"segments": nseg, "worst_err_over_bound" if op == "sum" else "mismatches":
+                worst if op == "sum" else sum(1 for e, _ in errs if e), "ok": worst <= 1.0}
+
+    def close(self):
+        self.pool.shutdown()
+
+
 # --------------------------------------------------------------------------
 # Secondary forms (all on the same GPU, same run)
 # --------------------------------------------------------------------------
 
-FORM_GROUPS = ("plain", "precision", "illcond", "segmented", "fwdbwd", "axis", "scan", "linesearch")
+FORM_GROUPS = ("plain", "precision", "illcond", "segmented", "fwdbwd", "axis", "scan", "linesearch", "sweep")
 
 
-def forms(steps, warmup, peak, only=None, tune=True):
+def forms(steps, warmup, peak, only=None, tune=True, chk=None):
+    """Every form at its workload size.  With a Checker (the oracle leg),
+    each form's results are then checked against the oracle: the record's
+    "check" entry."""
     import numpy as np
     import torch
     from paper_1710_07358_gb300 import pr, synth
@@ -184,11 +303,23 @@ def forms(steps, warmup, peak, only=None, tune=True):
     dev = torch.device("cuda")
     g = torch.Generator(device=dev)
 
-    def plain(name, t, op, **kw):
+    def plain(name, t, op, dtype=None, **kw):
         nb = t.numel() * t.element_size()
-        _, per = time_launches(lambda: pr.reduce(t, op, **kw), k, warmup, st)
+        out = pr.reduce(t, op, **kw)
+        _, per = time_launches(lambda: pr.reduce(t, op, out=out, **kw), k, warmup, st)
         res[name] = {"GB/s": round(gbs(nb, per), 1), "frac": round(gbs(nb, per) / peak, 4),
                      "us": round(per * 1e3, 2)}
+        if chk is not None:
+            torch.cuda.synchronize()
+            got = chk.value(out)
+            x = chk.host(t)
+            d = dtype or pr.dtype_name(t)
+            if op == "sum" and d in ("f32", "f16", "bf16"):
+                res[name]["check"] = chk.sum(x, d, got, kw.get("precision", "plain"))
+            elif op == "prod" and d in ("f32", "f64"):
+                res[name]["check"] = chk.prod(x, d, got)
+            else:
+                res[name]["check"] = chk.exact(x, d, op, got)
 
     want = set(only or FORM_GROUPS)
     n = N_HEAD
@@ -202,6 +333,10 @@ def forms(steps, warmup, peak, only=None, tune=True):
         _, per = time_launches(lambda: pr.reduce_arg(f32, "max"), k, warmup, st)
         res["f32_argmax"] = {"GB/s": round(gbs(nb, per), 1), "frac": round(gbs(nb, per) / peak, 4),
                              "us": round(per * 1e3, 2)}
+        if chk is not None:
+            v, i = pr.reduce_arg(f32, "max")
+            wv, wi = chk.oracle.argext(chk.host(f32), "f32", "max")
+            res["f32_argmax"]["check"] = {"exact": float(v.item()) == wv and int(i.item()) == wi}
         i32 = torch.randint(-(1 << 20), 1 << 20, (n,), generator=g, device=dev, dtype=torch.int32)
         for op in ("sum", "max", "min"):
             plain("i32_%s" % op, i32, op)
@@ -217,8 +352,8 @@ def forms(steps, warmup, peak, only=None, tune=True):
     if "precision" in want:
         for dt, name in ((torch.bfloat16, "bf16"), (torch.float16, "f16")):
             h = torch.randn(n, generator=g, device=dev).to(dt)
-            plain("%s_sum" % name, h, "sum")
-            plain("%s_sum_compensated" % name, h, "sum", precision="compensated")
+            plain("%s_sum" % name, h, "sum", dtype=name)
+            plain("%s_sum_compensated" % name, h, "sum", dtype=name, precision="compensated")
             del h
         plain("f32_sum_compensated", f32, "sum", precision="compensated")
         plain("f32_sum_fp64_combine", f32, "sum", precision="fp64_combine")
@@ -227,19 +362,97 @@ def forms(steps, warmup, peak, only=None, tune=True):
     if "illcond" in want:
         ill(res, k, warmup, peak, st)
     if "segmented" in want:
-        segmented(res, k, warmup, peak, tune)
+        segmented(res, k, warmup, peak, tune, chk)
     if "fwdbwd" in want:
-        fwdbwd(res, k, warmup, peak, st, g)
+        fwdbwd(res, k, warmup, peak, st, g, chk)
     if "axis" in want:
-        axis(res, k, warmup, peak, st, g)
+        axis(res, k, warmup, peak, st, g, chk)
     if "scan" in want:
-        scan(res, k, warmup, peak, st, g)
+        scan(res, k, warmup, peak, st, g, chk)
     if "linesearch" in want:
-        linesearch(res, k, warmup, peak, st, g)
+        linesearch(res, k, warmup, peak, st, g, chk)
+    if "sweep" in want:
+        sweep(res, k, warmup, peak, st, g)
     return res
 
 
-def scan(res, k, warmup, peak, st, g):
+SWEEP_SIZES = [1 << e for e in range(10, 31)] + [5_533_214]      # the paper's vector length last
+L2_BYTES = 129 << 20
+
+
+def sweep(res, k, warmup, peak, st, g):
+    """The plain fp32 sum from n = 2^10 to 2^30, and the paper's n = 5 533 214.
+
+    Below 4x L2 (n < 2^27) two numbers: "hot_us", the per-call time of a CUDA
+    graph of 64 back-to-back calls on L2-resident data (the latency regime);
+    and "cold_us" with L2 flushed before every call (a 512 MiB write outside
+    the timed region, followed by a 256 MiB read that evicts the written
+    lines), from which GB/s.  From 2^27 on the input is at least
+    4x L2 and calls are timed back to back.  Every n is a prefix of one 4 GiB
+    buffer (aligned like a fresh allocation)."""
+    import torch
+    from paper_1710_07358_gb300 import pr
+    dev = torch.device("cuda")
+    g.manual_seed(11)
+    big = torch.rand((1 << 30) + 64, generator=g, device=dev) * 2 - 1
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    evict = torch.empty(64 << 20, dtype=torch.float32, device=dev).fill_(1.0)
+    out = torch.empty((), dtype=torch.float32, device=dev)
+    rows = []
+    for n in SWEEP_SIZES:
+        x = big[:n]
+        nb = 4 * n
+        rec = {"n": n}
+        if nb < 4 * L2_BYTES:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                pr.prepare(s)
+                pr.reduce(x, "sum", out=out, stream=s)
+            s.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                for _ in range(64):
+                    pr.reduce(x, "sum", out=out, stream=s)
+            for _ in range(2):
+                graph.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                graph.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            rec["hot_us"] = round(e0.elapsed_time(e1) * 1e3 / (5 * 64), 3)
+            per = []
+            for _ in range(k + warmup):
+                # flush: a 512 MiB write, then a 256 MiB read that evicts its
+                # dirty lines, so no write-back overlaps the timed call
+                flush.zero_()
+                evict.sum()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                pr.reduce(x, "sum", out=out)
+                b.record(st)
+                per.append((a, b))
+            torch.cuda.synchronize()
+            # the mean: single event pairs tick in steps of about 2 us, and
+            # the launches' phase against those steps varies
+            cold = [a.elapsed_time(b) for a, b in per[warmup:]]
+            ms = sum(cold) / len(cold)
+            rec["cold_us"] = round(ms * 1e3, 3)
+        else:
+            _, ms = time_launches(lambda: pr.reduce(x, "sum", out=out), k, warmup, st)
+            rec["us"] = round(ms * 1e3, 2)
+        rec["GB/s"] = round(gbs(nb, ms), 1)
+        rec["frac"] = round(gbs(nb, ms) / peak, 4)
+        rows.append(rec)
+    res["sweep_f32_sum"] = {"l2_rule": "n*4 < 4 x 129 MB: 512 MiB write + 256 MiB read before each cold call; "
+                                       "hot = CUDA graph of 64 calls on L2-resident data",
+                            "points": rows}
+    del big, flush, evict
+
+
+def scan(res, k, warmup, peak, st, g, chk=None):
     """One-pass prefix scans of n = 2^28 (or the --n-log2 size): uint32 sum (offsets of a counting
     sort: 1 GiB read + 1 GiB written), int32 sum widening to int64 (1 GiB read,
     2 GiB written) and fp32 running max (1 GiB + 1 GiB).  Bandwidth counts the
@@ -260,18 +473,31 @@ def scan(res, k, warmup, peak, st, g):
     _, per = time_launches(lambda: pr.check(pr.pr_scan(xu.data_ptr(), n, pr.DTYPES["u32"], pr.OPS["sum"], 1,
                                                        yu.data_ptr(), st.cuda_stream)), k, warmup, st)
     put("scan_u32_sum_exclusive", per, 2 * n * 4)
+    import numpy as np
+    if chk is not None:                              # every element against the oracle's loop
+        xh = chk.host(xi)
+        want = chk.oracle.scan(xh.view(np.uint32), "u32", "sum", True)
+        res["scan_u32_sum_exclusive"]["check"] = {"exact": bool(np.array_equal(chk.host(yu).view(np.uint32), want))}
+        del want
     y64 = torch.empty(n, dtype=torch.int64, device=dev)
     _, per = time_launches(lambda: pr.scan(xi, "sum", out=y64), k, warmup, st)
     put("scan_i32_sum_to_i64", per, n * 4 + n * 8)
+    if chk is not None:
+        res["scan_i32_sum_to_i64"]["check"] = {
+            "exact": bool(np.array_equal(chk.host(y64), chk.oracle.scan(xh, "i32", "sum", False)))}
+        del xh
     del y64, yu
     xf = torch.randn(n, generator=g, device=dev)
     yf = torch.empty_like(xf)
     _, per = time_launches(lambda: pr.scan(xf, "max", out=yf), k, warmup, st)
     put("scan_f32_max", per, 2 * n * 4)
+    if chk is not None:
+        res["scan_f32_max"]["check"] = {"exact": bool(np.array_equal(
+            chk.host(yf).astype(np.float64), chk.oracle.scan(chk.host(xf), "f32", "max", False)))}
     del xf, yf, xi
 
 
-def linesearch(res, k, warmup, peak, st, g):
+def linesearch(res, k, warmup, peak, st, g, chk=None):
     """Golden-section (tolerance 1e-6 on [0, 1]: 29 iterations) and Fibonacci
     (31 evaluations) search of the Beckmann objective (BPR, beta 0.15, power
     4) over 2^24 synthetic links: four float32 arrays, 256 MiB per pass, more
@@ -310,10 +536,24 @@ def linesearch(res, k, warmup, peak, st, g):
             res["linesearch_%s_d%d" % (method, depth)] = {
                 "us": round(per * 1e3, 1), "passes": passes, "GB/s": round(gbs(nb * passes, per), 1),
                 "frac": round(gbs(nb * passes, per) / peak, 4), "alpha": round(float(out[2].item()), 7)}
+            if chk is not None and depth == 2:
+                # phi at the point the search kept, against the oracle's sum
+                # of float64 terms, within the evaluation's derived bound
+                import numpy as np
+                from oracle import linesearch as ols
+                arrs = [chk.host(v) for v in (x, d, t0, c)]
+                a32, b32 = float(np.float32(out[2].item())), float(np.float32(0.15))
+                want = ols.phi(*arrs, b32, 4, a32)
+                lin, pw = ols.phi_parts(*arrs, b32, 4, a32)
+                bound = 1.001 * 2.0 ** -24 * (8 * float(np.abs(lin).sum()) + 25 * float(np.abs(pw).sum()))
+                err = abs(float(out[3].item()) - want)
+                width = float(out[1].item()) - float(out[0].item())
+                res["linesearch_%s_d%d" % (method, depth)]["check"] = {
+                    "phi_abs_err": err, "bound": bound, "ok": err <= bound, "bracket_width": width}
     del x, d, t0, c
 
 
-def axis(res, k, warmup, peak, st, g):
+def axis(res, k, warmup, peak, st, g, chk=None):
     """Reductions of a non-last axis, 1 GiB each: the middle axis of
     [16, 4096, 4096] fp32 (sum; max with its first index) and its gradient,
     and the first axis of [16384, 16384] (a column reduction)."""
@@ -330,16 +570,40 @@ def axis(res, k, warmup, peak, st, g):
 
     _, per = time_launches(lambda: pr.reduce_axis(x, "sum", 1), k, warmup, st)
     put("axis_mid_sum", per, nb)
+    cols = [(0, 0), (5, 1234), (15, 4095)]           # sampled outputs (slab, column)
+    if chk is not None:
+        ys = pr.reduce_axis(x, "sum", 1)
+        worst = 0.0
+        for p, q in cols:
+            col = chk.host(x[p, :, q].contiguous())
+            r = chk.sum(col, "f32", float(ys[p, q].item()))
+            worst = max(worst, r["abs_err"] / r["bound"])
+        res["axis_mid_sum"]["check"] = {"sampled_outputs": len(cols), "worst_err_over_bound": worst,
+                                        "ok": worst <= 1.0}
     _, per = time_launches(lambda: pr.reduce_axis(x, "max", 1, argidx=True), k, warmup, st)
     put("axis_mid_max_arg", per, nb)
+    if chk is not None:
+        ym, yi = pr.reduce_axis(x, "max", 1, argidx=True)
+        ok = all(chk.oracle.argext(chk.host(x[p, :, q].contiguous()), "f32", "max") ==
+                 (float(ym[p, q].item()), int(yi[p, q].item())) for p, q in cols)
+        res["axis_mid_max_arg"]["check"] = {"sampled_outputs": len(cols), "exact": ok}
     gout = torch.randn(16, 4096, generator=g, device=dev)
     gi = torch.empty_like(x)
     _, per = time_launches(lambda: pr.reduce_axis_backward("sum", x, 1, gout, out=gi), k, warmup, st)
     put("axis_mid_sum_bwd", per, nb)
+    if chk is not None:                              # d(sum)/dx = grad_out broadcast along the axis, exactly
+        res["axis_mid_sum_bwd"]["check"] = {"exact": bool(torch.equal(gi, gout[:, None, :].expand_as(gi)))}
     del x, gi
     c = torch.randn(16384, 16384, generator=g, device=dev)
     _, per = time_launches(lambda: pr.reduce_axis(c, "sum", 0), k, warmup, st)
     put("axis_col_sum", per, c.numel() * 4)
+    if chk is not None:
+        yc = pr.reduce_axis(c, "sum", 0)
+        worst = 0.0
+        for q in (0, 7777, 16383):
+            r = chk.sum(chk.host(c[:, q].contiguous()), "f32", float(yc[q].item()))
+            worst = max(worst, r["abs_err"] / r["bound"])
+        res["axis_col_sum"]["check"] = {"sampled_outputs": 3, "worst_err_over_bound": worst, "ok": worst <= 1.0}
     del c
 
 
@@ -362,13 +626,15 @@ def ill(res, k, warmup, peak, st):
     errs = {}
     for prec in ("plain", "fp64_combine", "compensated"):
         v = pr.reduce(xt, "sum", precision=prec).item()
-        errs[prec] = {"result": v, "abs_err": abs(v - exact), "err_over_sum_abs": abs(v - exact) / abs_sum}
+        bound = (2.0 ** -24 if prec == "compensated" else 1e-6) * abs_sum
+        errs[prec] = {"result": v, "abs_err": abs(v - exact), "err_over_sum_abs": abs(v - exact) / abs_sum,
+                      "bound": bound, "ok": abs(v - exact) <= bound}
     plain("f32_illcond_compensated", xt, "sum", precision="compensated")
     res["illcond_errors"] = {"n": 1 << 26, "exact": exact, "kappa": abs_sum / exact, **errs}
     del xt
 
 
-def segmented(res, k, warmup, peak, tune=True):
+def segmented(res, k, warmup, peak, tune=True, chk=None):
     import torch
     from paper_1710_07358_gb300 import pr, synth
     dev = torch.device("cuda")
@@ -395,10 +661,13 @@ def segmented(res, k, warmup, peak, tune=True):
         res["segmented_%s" % op] = {"GB/s": round(gbs(seg_bytes, per), 1), "frac": round(gbs(seg_bytes, per) / peak, 4),
                                     "us": round(per * 1e3, 2), "elements": int(vals.size), "config": cfg,
                                     "graph": True}
+        if chk is not None:
+            torch.cuda.synchronize()
+            res["segmented_%s" % op]["check"] = chk.segments(vals, off, op, out.cpu().numpy())
     del xv, ov
 
 
-def fwdbwd(res, k, warmup, peak, st, g):
+def fwdbwd(res, k, warmup, peak, st, g, chk=None):
     import torch
     from paper_1710_07358_gb300 import pr
     dev = torch.device("cuda")
@@ -436,6 +705,37 @@ def fwdbwd(res, k, warmup, peak, st, g):
                                   "fwd_bwd_GB/s": round(gbs(2 * mat, pf + pb), 1),
                                   "frac": round(gbs(2 * mat, pf + pb) / peak, 4),
                                   "us": round((pf + pb) * 1e3, 2)}
+        if chk is not None:
+            res["fwd_bwd_%s" % op]["check"] = fwdbwd_check(chk, op, xin, go, gi)
+
+
+def fwdbwd_check(chk, op, xin, go, gi):
+    """Sampled rows of the forward against the oracle, and the backward by
+    the properties that fix it: sum -> grad_out broadcast; max -> one-hot at
+    the first argmax; prod (every row here has two or more zeros) -> 0."""
+    import torch
+    from paper_1710_07358_gb300 import pr
+    rows = (0, 31, 63)
+    if op == "sum":
+        y = pr.reduce_rows(xin, "sum")
+        worst = 0.0
+        for r in rows:
+            rr = chk.sum(chk.host(xin[r]), "f32", float(y[r].item()))
+            worst = max(worst, rr["abs_err"] / rr["bound"])
+        return {"sampled_rows": len(rows), "fwd_worst_err_over_bound": worst,
+                "bwd_exact": bool(torch.equal(gi, go[:, None].expand_as(gi))), "ok": worst <= 1.0}
+    if op == "max":
+        y, ai = pr.reduce_rows(xin, "max", argidx=True)
+        fwd_ok = all(chk.oracle.argext(chk.host(xin[r]), "f32", "max") == (float(y[r].item()), int(ai[r].item()))
+                     for r in rows)
+        onehot = torch.zeros_like(gi).scatter_(1, ai[:, None], go[:, None])
+        return {"sampled_rows": len(rows), "fwd_exact": fwd_ok, "bwd_exact": bool(torch.equal(gi, onehot))}
+    y, ax = pr.reduce_rows(xin, "prod", aux=True)
+    _, zc, zi = pr.prod_aux_fields(ax)
+    fwd_ok = all(chk.oracle.prod_aux(chk.host(xin[r]), "f32")[1:] == (int(zc[r].item()), int(zi[r].item()))
+                 for r in rows)
+    return {"sampled_rows": len(rows), "fwd_zero_count_and_index_exact": fwd_ok,
+            "fwd_all_zero": bool(torch.all(y == 0)), "bwd_all_zero": int(torch.count_nonzero(gi).item()) == 0}
 
 
 # --------------------------------------------------------------------------
@@ -533,7 +833,7 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_HEAD, "op": "sum", "dtype": "f32",
                                            "parallelism": "replicas" if world > 1 else "single",
                                            "l2": L2_NOTE},
-            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "model": cpu_model(),
                              "sample": "first %d elements of the n=2^28 workload per step" % m},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -621,18 +921,36 @@ def run_ours(args):
                        "l2": L2_NOTE, "launch": cfg},
             "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
             "result": res_val}
+    chk = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the CPU-baseline leg: the oracle and the chunked multi-core loop,
+        # timed on the host cores, then every GPU result of this run checked
+        # against the oracle
+        model = cpu_model()
         dt = cpu_oracle_sum(x_host)
         line["cpu_baseline"] = {"value": round(gbs(nbytes, dt * 1e3), 4), "unit": "GB/s", "cores": 1,
-                                "kind": "oracle",
+                                "kind": "oracle", "model": model,
                                 "sample": "whole n=2^28 workload once (exact fixed-point sum, one core)"}
+        mt, cores = cpu_chunked_baseline(x_host)
+        line["cpu_baseline_multicore"] = {"value": round(mt, 2), "unit": "GB/s", "cores": cores,
+                                          "kind": "Algorithm 1 per contiguous chunk, float64 accumulators, "
+                                                  "chunk sums in order", "model": model,
+                                          "sample": "whole n=2^28 workload, best of 5"}
         import oracle
         line["abs_err_vs_exact"] = oracle.sum_error(x_host, "f32", res_val)
         line["err_bound_1e-6_sum_abs"] = 1e-6 * oracle.abs_sum(x_host, "f32")
+        chk = Checker()
     if rank == 0 and world == 1 and not args.no_forms:
         del x
         torch.cuda.empty_cache()
-        line["forms"] = forms(args.steps, args.warmup, peak, tune=not args.no_tune)
+        line["forms"] = forms(args.steps, args.warmup, peak, tune=not args.no_tune, chk=chk)
+    if chk is not None:
+        chk.close()
+        bad = sorted(k for k, v in line.get("forms", {}).items() if isinstance(v, dict) and "check" in v and
+                     not all(v["check"].get(f, True) for f in ("ok", "exact", "fwd_exact", "bwd_exact",
+                                                                "fwd_zero_count_and_index_exact",
+                                                                "fwd_all_zero", "bwd_all_zero")))
+        line["checks_failed"] = bad
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so next to it (gcc, ISO C, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC) or _foreign(_LIB):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
                                _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -71,6 +71,7 @@ def _L():
             "orc_exact_abs_sum": (D, [P, I64, I]),
             "orc_exact_sum_minus": (D, [P, I64, I, D]),
             "orc_sum_f64_loop": (D, [P, I64, I]),
+            "orc_sum_f64_chunked": (D, [P, I64, I, I]),
             "orc_reduce_int": (I, [P, I64, I, I, P]),
             "orc_argext": (I, [P, I64, I, I, PD, PI64]),
             "orc_argext_int": (I, [P, I64, I, I, PI64]),
@@ -175,6 +176,14 @@ def sum_f64_loop(x, dtype: str) -> float:
     """Algorithm 1 verbatim: a double accumulator, elements added in index order."""
     a = _arr(x, dtype)
     return _L().orc_sum_f64_loop(_ptr(a), a.size, DTYPES[dtype])
+
+
+def sum_f64_chunked(x, dtype: str, threads: int) -> float:
+    """Algorithm 1 per contiguous chunk on `threads` host threads (double
+    accumulators), the chunk sums added in chunk order: the multi-core CPU
+    baseline.  The C loops run with the GIL released."""
+    a = _arr(x, dtype)
+    return _L().orc_sum_f64_chunked(_ptr(a), a.size, DTYPES[dtype], int(threads))
 
 
 def exact_sum(x, dtype: str) -> float:

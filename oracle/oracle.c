@@ -13,6 +13,9 @@
  *   orc_reduce_int      integer/bitwise combiners, exact (two's-complement
  *                       wrap-around where the output type wraps).
  *   orc_sum_f64_loop    Algorithm 1 verbatim with a double accumulator.
+ *   orc_sum_f64_chunked the same loop over contiguous chunks on several host
+ *                       threads, chunk sums added in order (the multi-core
+ *                       CPU baseline the benchmark times beside the GPU).
  *   orc_exact_sum       the exact sum of the inputs (every binary16/bfloat16/
  *                       binary32/binary64 value is an integer multiple of
  *                       2^-1074, so a fixed-point accumulator of 32-bit limbs
@@ -35,7 +38,7 @@
  *                       after every step.  Integer/bitwise combiners and float
  *                       max/min (the combiners whose result is exact).
  *
- * Build: gcc -std=c11 -O2 -ffp-contract=off -fPIC -shared (ISO C, no FMA
+ * Build: gcc -std=c11 -O2 -ffp-contract=off -fPIC -shared -pthread (ISO C, no FMA
  * contraction, so that x86-64 and AArch64 hosts give identical results).
  */
 #include <stdint.h>
@@ -199,6 +202,52 @@ double orc_exact_sum_minus(const void* x, int64_t n, int dtype, double r) {
 double orc_sum_f64_loop(const void* x, int64_t n, int dtype) {
     double acc = 0.0;
     for (int64_t i = 0; i < n; i++) acc = acc + elem_as_double(x, i, dtype);
+    return acc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Multi-core CPU baseline: Algorithm 1 per chunk, chunks in order.     */
+/* ------------------------------------------------------------------ */
+
+/* The input is cut into `nthreads` contiguous chunks of (nearly) equal
+ * length; thread k runs Algorithm 1 with a double accumulator over chunk k,
+ * and the chunk sums are then added in chunk order.  With one thread this is
+ * orc_sum_f64_loop.  This is the timed multi-core CPU baseline, not a
+ * reference value: its error is that of a double summation (within
+ * (n - 1) 2^-53 sum |x| of the exact sum). */
+#include <pthread.h>
+
+typedef struct { const void* x; int64_t lo, hi; int dtype; double sum; } sum_chunk;
+
+static void* sum_chunk_run(void* arg) {
+    sum_chunk* c = (sum_chunk*)arg;
+    double acc = 0.0;
+    for (int64_t i = c->lo; i < c->hi; i++) acc = acc + elem_as_double(c->x, i, c->dtype);
+    c->sum = acc;
+    return NULL;
+}
+
+double orc_sum_f64_chunked(const void* x, int64_t n, int dtype, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    sum_chunk ch[256];
+    pthread_t th[256];
+    int started[256];
+    for (int k = 0; k < nthreads; k++) {
+        ch[k].x = x;
+        ch[k].lo = n * k / nthreads;
+        ch[k].hi = n * (k + 1) / nthreads;
+        ch[k].dtype = dtype;
+        ch[k].sum = 0.0;
+        started[k] = k > 0 && pthread_create(&th[k], NULL, sum_chunk_run, &ch[k]) == 0;
+    }
+    sum_chunk_run(&ch[0]);
+    for (int k = 1; k < nthreads; k++) {
+        if (started[k]) pthread_join(th[k], NULL);
+        else sum_chunk_run(&ch[k]);                 /* no thread: run it here */
+    }
+    double acc = 0.0;
+    for (int k = 0; k < nthreads; k++) acc = acc + ch[k].sum;
     return acc;
 }
 

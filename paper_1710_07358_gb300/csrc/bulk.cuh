@@ -1,0 +1,66 @@
+// Shared-memory staging by bulk copies: mbarrier helpers, a bounded barrier
+// wait and the global -> shared bulk copy, used by the kernels that keep a
+// ring of shared-memory stages filled ahead of their consumers (the prefix
+// scan and the line search's evaluation pass).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "kernels.cuh"
+
+namespace pr {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the completion of the phase with parity `par` of a
+// shared-memory barrier: false after `limit_ns` (setting *abort_flag and
+// kErrTimeout in the error word) or as soon as *abort_flag is set.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, unsigned par, unsigned long long limit_ns,
+                                         volatile int* abort_flag, int* err) {
+    if (mbar_try_wait(bar, par)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, par)) {
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > limit_ns) {
+            *abort_flag = 1;
+            atomicOr(err, kErrTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+// global -> shared, completion counted in bytes on the barrier; both
+// addresses 16-byte aligned, size a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, unsigned bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+}  // namespace pr

@@ -825,6 +825,10 @@ struct ProdAux {
     struct Acc { typename Base::Acc p; int64_t zi; uint32_t zc; uint32_t sx; };
     struct Part { typename Base::Part p; int64_t zc; int64_t zi; uint32_t sall; uint32_t pad_; };
     static constexpr bool kIdx = true;
+    // The zero handling lengthens each vector's dependent chain; compiled for
+    // at most 512 threads, the row kernel gets the registers to keep more of
+    // it in flight (measured on GB300, [64, 2^20] fp32: 52.8 -> 51.1 us).
+    static constexpr int kMaxBlock = 512;
     __device__ __forceinline__ static uint32_t sign_word(E v) {
         if constexpr (sizeof(E) == 8) return (uint32_t)((uint64_t)__double_as_longlong(v) >> 32);
         else return __float_as_uint(v);

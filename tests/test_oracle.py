@@ -475,3 +475,21 @@ def test_bandwidth_formula_reproduces_table2():
         assert abs(gbs(synth.PAPER_N * 4, float(t_ms) * 1e-3) - float(bw)) < 1e-6
         # the usage column is bandwidth / a peak of ~332.8 GB/s
         assert abs(float(bw) / 332.75 * 100 - float(pct)) < 0.02
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 8, 17])
+def test_chunked_multicore_baseline(threads):
+    """The multi-core CPU baseline: one thread is Algorithm 1 itself; integer
+    valued inputs sum exactly in any order and any chunking; otherwise the
+    result lies within the worst case of any double summation order,
+    (n - 1) 2^-53 sum |x|, of the exact sum."""
+    n = 100003
+    x = np.random.default_rng(threads).uniform(-1, 1, n).astype(np.float32)
+    got = oracle.sum_f64_chunked(x, "f32", threads)
+    if threads == 1:
+        assert got == oracle.sum_f64_loop(x, "f32")
+    assert abs(got - oracle.exact_sum(x, "f32")) <= (n - 1) * 2.0 ** -53 * oracle.abs_sum(x, "f32")
+    ints = np.random.default_rng(threads + 50).integers(-1000, 1000, n).astype(np.float32)
+    assert oracle.sum_f64_chunked(ints, "f32", threads) == float(ints.astype(np.int64).sum())
+    assert oracle.sum_f64_chunked(x[:0], "f32", threads) == 0.0
+    assert oracle.sum_f64_chunked(x[:5], "f32", threads) == pytest.approx(float(x[:5].astype(np.float64).sum()))
