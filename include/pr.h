@@ -35,7 +35,9 @@
  *   - F64 PROD keeps a separate integer exponent, so no partial product
  *     overflows or underflows; half of each vector's factors multiply on the
  *     fp64 pipe (rounded to nearest), half as 64-bit integer significands
- *     (truncated, under 2^-61 each): within (n - 1) 2^-53 relative.
+ *     (truncated, under 2^-61 each).  Of the n - 1 merges of partial
+ *     products at most n / 2 round to nearest, the others truncate, and the
+ *     conversion to double rounds once: within max(n - 1, 2) 2^-53 relative.
  *
  * Result types (pr_out_dtype):
  *   F32 -> F32;  F16/BF16: SUM,PROD -> F32, MAX,MIN -> same type;  F64 -> F64;

@@ -9,9 +9,17 @@
 // Zeros, infinities, NaNs and subnormals always take the integer path, which
 // records their class.  The two partial products meet in to_part.
 //
-// Error: an fp64 multiply rounds to nearest (2^-53 relative), an integer-pipe
-// step truncates (under 2^-61), so n factors err by less than
-// n / 2 * (2^-53 + 2^-61), inside the (n - 1) * 2^-53 of any evaluation order.
+// Error, every rounding counted (first order, u = 2^-53).  Whatever the order,
+// combining n factors takes exactly n - 1 merges of two partial products that
+// both hold factors (a merge with the identity -- an untouched accumulator,
+// or the 1.0 an fp64-pipe product starts from -- is exact).  A merge on the
+// fp64 pipe rounds to nearest (at most u); a merge on the integer pipes
+// (mul_sig: per factor, in to_part, fold, and the warp, block and grid
+// combines) truncates, under 3 * 2^-63 < u / 256.  At most n / 2 merges run
+// on the fp64 pipe, and the final conversion to double rounds once more.  So
+// the relative error is below u (n / 2 + 1) + (u / 256) (n - 1), which is at
+// most max(n - 1, 2) u for every n (n <= 4 counted case by case: one vector
+// of four makes one rounding fp64 merge and two truncations).
 #pragma once
 #include "traits.cuh"
 

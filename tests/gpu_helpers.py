@@ -73,9 +73,12 @@ def sum_bound(x, dtype, precision="plain"):
 
 def prod_rel_bound(n, dtype):
     """Relative error allowed for a product of n values: (n-1) units in the last
-    place of the accumulation type (the worst case of any evaluation order)."""
-    u = 2.0 ** -53 if dtype == "f64" else 2.0 ** -24
-    return max(n - 1, 1) * u
+    place of the accumulation type (the worst case of any evaluation order);
+    fp64 products also round once converting their 64-bit significand to
+    double, covered by max(n - 1, 2)."""
+    if dtype == "f64":
+        return max(n - 1, 2) * 2.0 ** -53
+    return max(n - 1, 1) * 2.0 ** -24
 
 
 # ---------------------------------------------------------------------------
