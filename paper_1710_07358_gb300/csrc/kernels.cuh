@@ -151,6 +151,17 @@ struct MaxBlock<T, std::void_t<decltype(T::kMaxBlock)>> {
     static constexpr int value = T::kMaxBlock;
 };
 
+// Blocks of the plain reduction that must fit on one SM at once (a trait
+// declares kMinBlocks to cap its registers per thread; default 1).
+template <class T, class = void>
+struct MinBlocks {
+    static constexpr int value = 1;
+};
+template <class T>
+struct MinBlocks<T, std::void_t<decltype(T::kMinBlocks)>> {
+    static constexpr int value = T::kMinBlocks;
+};
+
 template <class T>
 __device__ __forceinline__ typename T::Part* slot(char* base, int64_t i) {
     return reinterpret_cast<typename T::Part*>(base + i * kSlot);
@@ -170,7 +181,7 @@ __device__ __forceinline__ typename T::Part fold(typename T::Acc (&acc)[U]) {
 // ------------------------------------------------------------------------
 
 template <class T, int U, int VB>
-__global__ void __launch_bounds__(MaxBlock<T>::value) k_reduce(ReduceArgs a) {
+__global__ void __launch_bounds__(MaxBlock<T>::value, MinBlocks<T>::value) k_reduce(ReduceArgs a) {
     using Ld = typename T::Ld;
     using In = typename Ld::In;
     using E = typename Ld::E;

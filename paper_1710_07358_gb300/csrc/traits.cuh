@@ -172,7 +172,13 @@ struct SumF {
 // Compensated sum (Section 1.1, second footnote: Kahan-style compensation).
 // Per thread: kLanes independent fp32 (sum, compensation) pairs, element k of
 // a vector going to lane k mod kLanes (independent dependency chains), each
-// element added with TwoSum.  Lanes, threads and warps combine as fp32 pairs
+// element added with TwoSum.  16-bit inputs (twice the elements per byte
+// of fp32) take two lanes and a launch bound that keeps six 256-thread
+// blocks resident per SM (at most 42 registers a thread): the eight
+// operations an element costs are then hidden by more warps rather than by
+// more chains per warp (measured on GB300, 2^28 bf16: four lanes at 40
+// resident warps 94.9 us, two lanes at 48 warps 88.6 us; fp32, where four
+// lanes measured faster, keeps them: 157 vs 160 us).  Lanes, threads and warps combine as fp32 pairs
 // with Neumaier's algorithm.  Each block partial s + c then crosses blocks as
 // one fp64 value (GridPart) summed with plain fp64 adds, and the result is
 // rounded once.  fp64 stays out of the block because GB300 issues fp64 adds at
@@ -187,11 +193,14 @@ template <class Ld_>
 struct SumComp {
     using Ld = Ld_;
     using E = typename Ld::E;
-    static constexpr int kLanes = 4;
+    static constexpr bool kHalf = Ld::ES == 2;
+    static constexpr int kLanes = kHalf ? 2 : 4;
     struct Acc { float s[kLanes], c[kLanes]; };
     struct Part { float s, c; };
     using GridPart = double;
     static constexpr bool kIdx = false;
+    static constexpr int kMaxBlock = kHalf ? 256 : 1024;
+    static constexpr int kMinBlocks = kHalf ? 6 : 1;
     __device__ __forceinline__ static Acc init() {
         Acc a;
 #pragma unroll
