@@ -181,7 +181,7 @@ __device__ __forceinline__ typename T::Part fold(typename T::Acc (&acc)[U]) {
 // ------------------------------------------------------------------------
 
 template <class T, int U, int VB>
-__global__ void __launch_bounds__(MaxBlock<T>::value, MinBlocks<T>::value) k_reduce(ReduceArgs a) {
+__device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
     using Ld = typename T::Ld;
     using In = typename Ld::In;
     using E = typename Ld::E;
@@ -246,6 +246,25 @@ __global__ void __launch_bounds__(MaxBlock<T>::value, MinBlocks<T>::value) k_red
         }
         *a.ws.counter = 0u;
     }
+}
+
+// The plain reduction's kernel.  A trait that declares kMinBlocks gets the
+// two-argument launch bound (a register cap); the others keep the one-argument
+// bound, with which the compiler chooses their registers freely (an explicit
+// minimum of one block makes it take more, and so halves some traits'
+// occupancy).
+template <class T, int U, int VB>
+__global__ void __launch_bounds__(MaxBlock<T>::value) k_reduce(ReduceArgs a) {
+    reduce_body<T, U, VB>(a);
+}
+template <class T, int U, int VB>
+__global__ void __launch_bounds__(MaxBlock<T>::value, MinBlocks<T>::value) k_reduce_occ(ReduceArgs a) {
+    reduce_body<T, U, VB>(a);
+}
+template <class T, int U, int VB>
+constexpr auto reduce_kernel() {
+    if constexpr (MinBlocks<T>::value > 1) return &k_reduce_occ<T, U, VB>;
+    else return &k_reduce<T, U, VB>;
 }
 
 // One block: out = parts[0] (x) parts[1] (x) ... in index order (slot stride kSlot).

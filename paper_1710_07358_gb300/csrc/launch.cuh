@@ -8,7 +8,7 @@ namespace pr {
 
 template <class T, int U, int VB>
 cudaError_t launch_reduce(const ReduceArgs& a, int grid, int block, cudaStream_t st) {
-    k_reduce<T, U, VB><<<grid, block, 0, st>>>(a);
+    reduce_kernel<T, U, VB>()<<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -52,7 +52,7 @@ template <class T, int U, int VB>
 void reg_one(uint8_t dtype, uint8_t op, uint8_t prec, uint8_t aux, bool plain, bool seg) {
     if (plain) {
         reg_add(KernelKey{K_REDUCE, dtype, op, prec, aux, (uint8_t)U, (uint8_t)VB},
-                KernelEntry{reinterpret_cast<const void*>(&k_reduce<T, U, VB>),
+                KernelEntry{reinterpret_cast<const void*>(reduce_kernel<T, U, VB>()),
                             reinterpret_cast<void*>(&launch_reduce<T, U, VB>)});
     }
     if (seg) {
