@@ -545,7 +545,7 @@ def linesearch(res, k, warmup, peak, st, g, chk=None):
                 a32, b32 = float(np.float32(out[2].item())), float(np.float32(0.15))
                 want = ols.phi(*arrs, b32, 4, a32)
                 lin, pw = ols.phi_parts(*arrs, b32, 4, a32)
-                bound = 1.001 * 2.0 ** -24 * (8 * float(np.abs(lin).sum()) + 25 * float(np.abs(pw).sum()))
+                bound = 1.001 * 2.0 ** -24 * (8 * float(np.abs(lin).sum()) + 29 * float(np.abs(pw).sum()))
                 err = abs(float(out[3].item()) - want)
                 width = float(out[1].item()) - float(out[0].item())
                 res["linesearch_%s_d%d" % (method, depth)]["check"] = {

@@ -245,7 +245,7 @@ pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream);
  * thread's links summed pairwise per point into a Kahan (sum, compensation)
  * pair, then combined in float64 in a fixed order: deterministic.  Error,
  * with u = 2^-24, counted from the operations (first order): each term's
- * linear part t0 v within 3 u, its power part within c u (c = 20 for power
+ * linear part t0 v within 3 u, its power part within c u (c = 24 for power
  * 4, else 4 power + 7), the sums within 5 u of sum |term|; so phi is within
  * u (8 sum |t0 v_i| + (c + 5) sum |power part_i|) <= (c + 5) u sum |term|
  * of the exact sum of the exact terms at float32(alpha) and beta.

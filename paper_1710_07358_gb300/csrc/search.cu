@@ -14,11 +14,13 @@
 //            combine order).  Error (u = 2^-24, first order): the linear
 //            part t0 v of a term takes three roundings (the fma placing v,
 //            the fma or product adding t0, the final product); the power
-//            part twenty at power 4 (B: ten; v^4: four on v and three of its
-//            own; the fma and the product) and 4 p + 7 otherwise; the sums
-//            five (three pairwise levels, two for Kahan's update), the
-//            float64 combines below 2^-45.  So phi is within
-//            u (8 sum |t0 v| + (c_p + 5) sum |power part|).
+//            part 24 u at power 4 (B: fourteen, the approximate reciprocal's
+//            2 u four times over, its two squarings, beta / 5, t0 kb and the
+//            last product; v^4: four on v and three of its own; the fma and
+//            the product) and (4 p + 7) u otherwise; the sums five (three
+//            pairwise levels, two for Kahan's update), the float64 combines
+//            below 2^-45.  So phi is within
+//            u (8 sum |t0 v| + (c_p + 5) sum |power part|), c_4 = 24.
 // k_ls_init  places the first two points and the speculative tree.
 // ls_step    (one thread of a search pass's last block, after the sums) walks
 //            depth D decisions with the values of the pass, then places the
@@ -68,11 +70,14 @@ __device__ __forceinline__ void phi_group(const float (&X)[L], const float (&D)[
     float inv[L], bc[L];
 #pragma unroll
     for (int l = 0; l < L; l++) {
-        inv[l] = __frcp_rn(C[l]);
         if constexpr (PW == 4) {
+            // rcp.approx: within one unit in the last place (PTX ISA), one
+            // instruction; only B depends on it
+            asm("rcp.approx.f32 %0, %1;" : "=f"(inv[l]) : "f"(C[l]));
             const float i2 = inv[l] * inv[l];
             bc[l] = (T[l] * kb) * (i2 * i2);
         } else {
+            inv[l] = __frcp_rn(C[l]);
             bc[l] = T[l] * kb * C[l];
         }
     }

@@ -24,15 +24,16 @@ def eval_bound(arrs, p, a32):
     (u = 2^-24, first order, times 1.001 for the higher-order terms):
       linear part t0 v:   v = fma(alpha, d, x), fma(B, v^4, t0) or t0 * v,
                           the last product or fma: 3 u
-      power part:         power 4 (B = t0 (beta / 5) rcp(c)^4, v^4 by two
-                          squarings, fma, product): 20 u; other powers
-                          (rcp(c), q = v rcp(c), p products, t0 kb c, fma):
-                          4 p + 7 u
+      power part:         power 4 (B = t0 (beta / 5) rcp(c)^4 with an
+                          approximate reciprocal within 2 u, v^4 by two
+                          squarings, fma, product): 24 u; other powers (a
+                          correctly rounded rcp(c), q = v rcp(c), p products,
+                          t0 kb c, fma): 4 p + 7 u
       summation:          eight terms pairwise (3 u), Kahan (2 u), float64
                           combines (below 2^-45): 5 u of sum |term|
     so |phi_gpu - phi| <= u (8 sum |t0 v| + (c_p + 5) sum |power part|)."""
     lin, pw = ols.phi_parts(*arrs, B32, p, a32)
-    cp = 20 if p == 4 else 4 * p + 7
+    cp = 24 if p == 4 else 4 * p + 7
     # numpy's pairwise float64 sums of non-negative values err by far less
     # than the 2^-40 added here, so the bound stays an upper bound
     up = 1.0 + 2.0 ** -40
