@@ -16,11 +16,16 @@ with the oracle:
   batching      4096 log-uniform segments (about 3.15e8 fp32 values), sum and
                 max, every segment, with the table's launch shape and after
                 the autotuner, replayed from a CUDA graph
+  prefix scan   n = 2^28: uint32 exclusive sum, int32 sum widening to int64,
+                fp32 running max, every element
+  any axis      the middle axis of [16, 4096, 4096] (sum; max with its index;
+                the sum's gradient) and the first axis of [16384, 16384] (sum),
+                1 GiB each, on sampled outputs
 
 Integer, bitwise and max / min results are compared bit for bit; float sums
 by their exact error against the bounds stated in include/pr.h (1e-6 sum|x|
 plain, 2^-24 sum|x| compensated); the fp64 product by its relative error
-against (n - 1) 2^-53.  The differentiation workload ([64, 2^20]) is checked
+against max(n - 1, 2) 2^-53.  The differentiation workload ([64, 2^20]) is checked
 at full size in test_gpu_autograd.py.
 """
 import numpy as np
@@ -271,3 +276,52 @@ def test_segmented_4096_log_uniform_every_segment():
             assert pr.last_device_error() == 0
         finally:
             pr.set_config("segmented", "f32", op, "plain", 4096, old)
+
+
+# ---------------------------------------------------------------------------
+# the next rows at their benchmark sizes: prefix scans of 2^28 elements and
+# the 1 GiB axis reductions
+# ---------------------------------------------------------------------------
+
+def test_scans_2e28_every_element():
+    import torch
+    xi = synth.uniform_i32(N, synth.config_seed(6), 0, 1 << 8)     # counting-sort offsets
+    t = dev(xi)
+    y = pr.scan(t.view(torch.uint32), "sum", exclusive=True)
+    got = y.view(torch.int32).cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, oracle.scan(xi.view(np.uint32), "u32", "sum", True))
+    del y, got
+    y64 = pr.scan(t, "sum")
+    assert np.array_equal(y64.cpu().numpy(), oracle.scan(xi, "i32", "sum", False))
+    del y64, t
+    xf = synth.normal_f32(N, synth.config_seed(6) + 1)
+    yf = pr.scan(dev(xf), "max").cpu().numpy()
+    assert np.array_equal(yf.astype(np.float64), oracle.scan(xf, "f32", "max", False))
+
+
+def test_axis_1gib_shapes_sampled_outputs():
+    import torch
+    shape = (16, 4096, 4096)
+    x = synth.normal_f32(16 * 4096 * 4096, synth.config_seed(5))
+    t = dev(x).view(*shape)
+    s = pr.reduce_axis(t, "sum", 1).cpu().numpy()
+    m, ai = pr.reduce_axis(t, "max", 1, argidx=True)
+    m, ai = m.cpu().numpy(), ai.cpu().numpy()
+    xs = x.reshape(shape)
+    rng = np.random.default_rng(5)
+    picks = [(0, 0), (15, 4095), (7, 2048)] + [tuple(v) for v in zip(rng.integers(0, 16, 61), rng.integers(0, 4096, 61))]
+    for p, q in picks:
+        col = np.ascontiguousarray(xs[p, :, q])
+        assert oracle.sum_error(col, "f32", float(s[p, q])) <= sum_bound(col, "f32"), (p, q)
+        assert oracle.argext(col, "f32", "max") == (float(m[p, q]), int(ai[p, q])), (p, q)
+    g = torch.from_numpy(synth.normal_f32(16 * 4096, 55).reshape(16, 4096)).cuda()
+    gi = pr.reduce_axis_backward("sum", t, 1, g)
+    assert torch.equal(gi, g[:, None, :].expand(shape))
+    del t, gi
+    c = synth.normal_f32(16384 * 16384, synth.config_seed(5) + 1)
+    tc = dev(c).view(16384, 16384)
+    cs = pr.reduce_axis(tc, "sum", 0).cpu().numpy()
+    cm = c.reshape(16384, 16384)
+    for q in [0, 1, 8191, 16383] + list(rng.integers(0, 16384, 28)):
+        col = np.ascontiguousarray(cm[:, q])
+        assert oracle.sum_error(col, "f32", float(cs[q])) <= sum_bound(col, "f32"), q
