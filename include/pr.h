@@ -83,8 +83,8 @@ typedef enum {
  *   PLAIN          per-thread fp32 accumulators, fp32 combines (fp64 input: fp64).
  *   COMPENSATED    per-thread fp32 (sum, compensation) pairs, each element added
  *                  with its exact rounding error (TwoSum); pairs combined within
- *                  a block with Neumaier's algorithm in fp32; each block's s + c
- *                  summed across blocks in fp64; rounded once.
+ *                  and across blocks with Neumaier's algorithm in fp32; the final
+ *                  s + c rounded once.
  *   FP64_COMBINE   per-thread fp32 accumulators, fp64 warp/block/grid combine. */
 typedef enum {
     PR_PREC_PLAIN = 0, PR_PREC_COMPENSATED = 1, PR_PREC_FP64_COMBINE = 2
@@ -135,8 +135,8 @@ pr_status pr_reduce(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* ou
 
 /* As pr_reduce, with a precision mode for float SUM and a choice of output
  * type: out_dtype is pr_out_dtype(dtype, op), or PR_F64 for a float SUM under
- * COMPENSATED / FP64_COMBINE (the fp64 combined value, before the final
- * rounding).  Non-PLAIN precision with any other (dtype, op):
+ * COMPENSATED / FP64_COMBINE (the combined value in fp64, before the final
+ * rounding to fp32).  Non-PLAIN precision with any other (dtype, op):
  * PR_ERR_UNSUPPORTED.                          (Section 1.1, second footnote) */
 pr_status pr_reduce_ex(const void* x, int64_t n, pr_dtype dtype, pr_op op,
                        pr_precision precision, pr_dtype out_dtype, void* out,

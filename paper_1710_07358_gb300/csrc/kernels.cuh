@@ -111,11 +111,9 @@ struct BwdArgs {
 };
 
 
-// The value that crosses blocks.  By default a block's partial crosses as the
-// trait's Part; a trait may declare a wider GridPart (with to_grid, grid_init,
-// grid_combine, grid_store) used only for combining block partials -- the
-// compensated sum keeps fp32 pairs inside a block and combines blocks in fp64.
-template <class T, class = void>
+// The value that crosses blocks: the trait's Part, combined with the trait's
+// combine (the same one the warp and block stages use).
+template <class T>
 struct GridR {
     using Part = typename T::Part;
     __device__ __forceinline__ static Part up(const typename T::Part& p) { return p; }
@@ -126,17 +124,6 @@ struct GridR {
     __device__ __forceinline__ static void store_aux(int64_t* ai, pr_prod_aux* ax, int64_t i, const Part& p, int64_t sb) {
         T::store_aux(ai, ax, i, p, sb);
     }
-};
-
-template <class T>
-struct GridR<T, std::void_t<typename T::GridPart>> {
-    using Part = typename T::GridPart;
-    __device__ __forceinline__ static Part up(const typename T::Part& p) { return T::to_grid(p); }
-    __device__ __forceinline__ static Part part_init() { return T::grid_init(); }
-    __device__ __forceinline__ static Part combine(const Part& a, const Part& b) { return T::grid_combine(a, b); }
-    __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<GridR>(p); }
-    __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) { T::grid_store(out, i, p, f64); }
-    __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
 };
 
 // Largest block a trait's kernels are compiled for (a trait with a large

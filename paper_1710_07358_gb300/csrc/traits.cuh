@@ -178,17 +178,15 @@ struct SumF {
 // operations an element costs are then hidden by more warps rather than by
 // more chains per warp (measured on GB300, 2^28 bf16: four lanes at 40
 // resident warps 94.9 us, two lanes at 48 warps 88.6 us; fp32, where four
-// lanes measured faster, keeps them: 157 vs 160 us).  Lanes, threads and warps combine as fp32 pairs
-// with Neumaier's algorithm.  Each block partial s + c then crosses blocks as
-// one fp64 value (GridPart) summed with plain fp64 adds, and the result is
-// rounded once.  fp64 stays out of the block because GB300 issues fp64 adds at
-// ~0.5e12/s (inside the block it would cost more than the whole HBM stream),
-// and the cross-block sum uses single fp64 adds rather than fp64 Neumaier
-// because each fp64 operation of the finishing block's dependent chain costs
-// ~0.5 us there (measured: an fp64 Neumaier tree over 760 block partials took
-// 7 us after the last block's loop, one add per level 2.5 us).  With at most a
-// few thousand partials the fp64 sum errs by < 2^-40 of the sum of |partials|,
-// far inside the compensated bound 2^-24 * sum|x|.
+// lanes measured faster, keeps them: 157 vs 160 us).  Lanes, threads, warps
+// and blocks combine as fp32 pairs with Neumaier's algorithm, and the final
+// s + c is formed in fp64 and rounded once to the output type.  fp64 stays
+// off the path: GB300 issues fp64 adds at ~0.5e12/s, and each fp64 operation
+// of the finishing block's dependent chain cost ~0.5 us there (an fp64
+// Neumaier tree over 760 block partials took 7 us after the last block's
+// loop, plain fp64 adds 2.5 us, the fp32 pairs less: 157.5 -> 155.8 us at
+// 2^28).  The pairs also keep more bits than one fp64 sum of the block
+// partials did (the ill-conditioned set of 2^26: error 5.7e-6 before, 0 now).
 template <class Ld_>
 struct SumComp {
     using Ld = Ld_;
@@ -197,7 +195,6 @@ struct SumComp {
     static constexpr int kLanes = kHalf ? 2 : 4;
     struct Acc { float s[kLanes], c[kLanes]; };
     struct Part { float s, c; };
-    using GridPart = double;
     static constexpr bool kIdx = false;
     static constexpr int kMaxBlock = kHalf ? 256 : 1024;
     static constexpr int kMinBlocks = kHalf ? 6 : 1;
@@ -237,23 +234,21 @@ struct SumComp {
         return p;
     }
     __device__ __forceinline__ static Part warp_reduce(Part p) { return warp_combine<SumComp>(p); }
-    __device__ __forceinline__ static void grid_store(void* out, int64_t i, const GridPart& g, bool f64) {
-        if (f64) put_f64(out, i, g); else put_f32(out, i, (float)g);
-    }
+    // The final value: s + c in fp64 (its rounding, 2^-53 relative, is far
+    // below the final one), rounded once to the output type.
     __device__ __forceinline__ static void store(void* out, int64_t i, const Part& p, bool f64) {
-        grid_store(out, i, to_grid(p), f64);
+        const double v = value(p);
+        if (f64) put_f64(out, i, v); else put_f32(out, i, (float)v);
     }
     __device__ __forceinline__ static void store_aux(int64_t*, pr_prod_aux*, int64_t, const Part&, int64_t) {}
     __device__ __forceinline__ static void store_empty(void* out, int64_t i, bool f64, int64_t*, pr_prod_aux*) {
         store(out, i, part_init(), f64);
     }
     // Once an infinity enters, s stays +-inf or NaN and the compensation turns
-    // NaN; the partial is then s itself.
-    __device__ __forceinline__ static GridPart to_grid(const Part& p) {
+    // NaN; the value is then s itself.
+    __device__ __forceinline__ static double value(const Part& p) {
         return isfinite(p.s) ? (double)p.s + (double)p.c : (double)p.s;
     }
-    __device__ __forceinline__ static GridPart grid_init() { return 0.0; }
-    __device__ __forceinline__ static GridPart grid_combine(const GridPart& a, const GridPart& b) { return a + b; }
 };
 
 // fp64 input, fp64 sum.
