@@ -115,14 +115,27 @@ template <bool VEC, int PW, int MP>
 __global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 2 : 1) k_phi(PhiArgs a) {
     __shared__ double s_w[kPhiThreads / 32][kLsMaxPts];
     __shared__ bool s_last;
+    // A search's passes are launched as programmatic dependents of one
+    // another: the next pass may start as this one's blocks finish and issue
+    // its first loads of links, which no pass writes; it waits for this pass
+    // (griddepcontrol.wait: completed, its writes visible) before it reads
+    // the points this pass's last block places, and before it writes the
+    // partials and the ticket this pass's last block reads.  Without a
+    // programmatic launch both instructions return at once.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int m = a.m;
     float al[MP], s[MP], e[MP];
 #pragma unroll
     for (int k = 0; k < MP; k++) {
-        al[k] = k < m ? (float)a.pts[k] : 0.f;
+        al[k] = 0.f;
         s[k] = 0.f;
         e[k] = 0.f;
     }
+    auto points = [&]() {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < MP; k++) al[k] = k < m ? (float)a.pts[k] : 0.f;
+    };
     const float kb = a.beta / (float)(a.power + 1);
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -150,6 +163,7 @@ __global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 2 : 1) k_phi(PhiArgs a)
         if (i + stride < n4) {
             float X[8], D[8], T[8], C[8];
             load8(i, X, D, T, C);
+            points();
             for (;;) {
                 const int64_t j = i + 2 * stride;
                 const bool more = j + stride < n4;
@@ -167,6 +181,9 @@ __global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 2 : 1) k_phi(PhiArgs a)
                 }
             }
         }
+        else {
+            points();
+        }
         if (i < n4) {
             const float4 X = __ldcs(x4 + i), D = __ldcs(d4 + i), T = __ldcs(t4 + i), C = __ldcs(c4 + i);
             const float Xa[4] = {X.x, X.y, X.z, X.w}, Da[4] = {D.x, D.y, D.z, D.w}, Ta[4] = {T.x, T.y, T.z, T.w},
@@ -174,6 +191,8 @@ __global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 2 : 1) k_phi(PhiArgs a)
             phi_group<PW, 4, MP>(Xa, Da, Ta, Ca, kb, a.power, al, m, s, e);
         }
         done = n4 * 4;
+    } else {
+        points();
     }
     for (int64_t i = done + tid; i < a.n; i += stride) {
         const float X[1] = {__ldcs(a.x + i)}, D[1] = {__ldcs(a.d + i)}, T[1] = {__ldcs(a.t0 + i)},
@@ -287,6 +306,7 @@ __device__ int ls_tree(LsState& s, const LsNode& root, int levels, int base) {
 }
 
 __global__ void k_ls_init(LsState* sp, double lo, double hi, int method, int count, int total, int depth) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // the first pass may start streaming
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     LsState& s = *sp;
     s.method = method;
@@ -378,10 +398,25 @@ const void* phi_kernel(bool vec, int power, int m) {
     return vec ? phi_fn<true, kLsMaxPts>(power) : phi_fn<false, kLsMaxPts>(power);
 }
 
+// A search's pass is launched as a programmatic dependent of the kernel
+// before it on the stream, which is always the search's own k_ls_init or
+// previous pass: neither writes the link arrays the pass reads before its
+// wait.  A lone evaluation (pr_beckmann) may follow a caller's kernel that
+// writes them, so it is launched in plain stream order.
 template <bool VEC, int MP>
 static void phi_go(const PhiArgs& a, int grid, cudaStream_t st) {
-    if (a.power == 4) k_phi<VEC, 4, MP><<<grid, kPhiThreads, 0, st>>>(a);
-    else k_phi<VEC, 0, MP><<<grid, kPhiThreads, 0, st>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kPhiThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = a.ls ? 1 : 0;
+    if (a.power == 4) cudaLaunchKernelEx(&cfg, k_phi<VEC, 4, MP>, a);
+    else cudaLaunchKernelEx(&cfg, k_phi<VEC, 0, MP>, a);
 }
 
 cudaError_t launch_phi(const PhiArgs& a, int grid, bool vec, cudaStream_t st) {
