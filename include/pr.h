@@ -272,7 +272,11 @@ pr_status pr_check_bounded_wait(int32_t polls, pr_stream_t stream);
  * state lives on the device (a per-stream buffer made on first use, outside
  * graph capture): nothing is synchronised, and result (device, 4 doubles:
  * final a, b, the better of the last two points, its phi) is written by the
- * last kernel of the call.  A search of P passes is P + 1 launches. */
+ * last kernel of the call.  A search of P passes is P + 1 launches; each
+ * pass is launched as a programmatic dependent of the launch before it (it
+ * starts streaming links while that one finishes, and waits for it before
+ * reading the points it placed), so the link arrays must not be written by
+ * other work while a search runs on them. */
 pr_status pr_beckmann(const float* x, const float* d, const float* t0, const float* cap, int64_t n, float beta,
                       int32_t power, const double* alphas, int32_t m, double* out, pr_stream_t stream);
 
