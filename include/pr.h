@@ -129,7 +129,13 @@ typedef struct {
 
 /* out[0] = x[0] (x) ... (x) x[n-1]                (Section 1.1; Sections 2.3, 3)
  * x: n elements of `dtype` (any alignment of the element type).  n >= 0;
- * x may be NULL only if n == 0.  out: one element of pr_out_dtype(dtype, op). */
+ * x may be NULL only if n == 0.  out: one element of pr_out_dtype(dtype, op).
+ * Inputs of 768 MiB and more keep the grid-stride loop for about nine tenths
+ * of their vectors; blocks claim the rest in tiles from a counter, so that
+ * SMs that stream faster take more of the end.  A tile's partial is stored
+ * by tile index and all partials are combined in a fixed order, so the result
+ * still depends only on the configuration, n and x's alignment, not on which
+ * block took which tile. */
 pr_status pr_reduce(const void* x, int64_t n, pr_dtype dtype, pr_op op, void* out,
                     pr_stream_t stream);
 
@@ -390,6 +396,17 @@ pr_status pr_reduce_noalloc(const void* x, int64_t n, pr_dtype dtype, pr_op op, 
  * Process-wide; not meant to be armed while other threads use the library. */
 typedef enum { PR_FAULT_NONE = 0, PR_FAULT_ALLOC = 1, PR_FAULT_LAUNCH = 2 } pr_fault_site;
 pr_status pr_debug_inject_fault(int32_t site, int32_t after, int32_t* pending);
+
+/* The launch that pr_reduce_ex (arg = 0; its configuration for n) or
+ * pr_reduce_arg (arg = 1) would make for these arguments on `stream`, without
+ * making it: *grid blocks of *block threads (either pointer may be NULL), and
+ * *tail_vectors, the vectors of the configuration's width past the
+ * grid-stride part that blocks claim in tiles (0: none; may be NULL).  Like
+ * the first reduction on a stream, it creates the stream's workspace.  A hook
+ * for tests and tuning, with no counterpart in the paper. */
+pr_status pr_debug_reduce_plan(const void* x, int64_t n, pr_dtype dtype, pr_op op, pr_precision precision,
+                               int32_t arg, pr_stream_t stream, int32_t* grid, int32_t* block,
+                               int64_t* tail_vectors);
 
 /* ---------------------------------------------------------------------- */
 /* Set-up, status and tuning                                                */

@@ -276,6 +276,20 @@ static pr_status occupancy(const void* fn, int block, int* bps, size_t smem = 0)
 }
 
 static std::map<const void*, int> g_maxthr;
+static std::map<const void*, size_t> g_local;
+
+// Bytes of local memory (register spills) a thread of `fn` uses.
+static size_t local_bytes(const void* fn) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_local.find(fn);
+    if (it != g_local.end()) return it->second;
+    cudaFuncAttributes fa;
+    size_t v = 0;
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) v = fa.localSizeBytes;
+    else cudaGetLastError();
+    g_local.emplace(fn, v);
+    return v;
+}
 
 // The configuration with its block size clamped to the kernel's compiled limit
 // (a trait with a large per-thread state compiles for at most 512 threads).
@@ -300,6 +314,48 @@ static pr_config fit_block(const KernelEntry* e, pr_config c) {
     return c;
 }
 
+// Claimed tail of the plain reduction.  SMs finish equal static shares of a
+// grid-stride loop a few microseconds apart (more, the longer the loop), so
+// a static split ends when the slowest SM does.  Inputs from kTailMinBytes
+// on leave about a tenth of their vectors (past a multiple of the grid's
+// stride) to tiles of about kTileBytes that blocks claim.  Measured on
+// GB300, fp32 sum, 1024 x 1 blocks, A/B in one process: 1 GiB 153.6 ->
+// 151.7 us, 4 GiB 580.2 -> 574.5 us; 512 MiB 82.0 -> 82.0 us and 256 MiB
+// 45.9 -> 47.4 us, where the tiles' barriers cost what the balance saves.
+// A fifth measured no better than a tenth, a twentieth worse.
+constexpr int64_t kTailMinBytes = (int64_t)3 << 28;
+constexpr int64_t kTileBytes = (int64_t)128 << 10;
+constexpr size_t kTailSpillSlack = 16;   // spill bytes a thread of the tail kernel may add
+// A tile is a run of rounds (a block's loads in flight at once); with rounds
+// under 32 KiB (256-thread blocks: fp32 max at 256 x 2, int32 sum at 256 x 4)
+// a tile's rounds cost more than the balance saves (174 / 167 us against
+// 153 / 158 us without), so such shapes keep the grid-stride kernel.
+constexpr int64_t kTailMinRound = (int64_t)32 << 10;
+
+static void tail_split(int64_t nafter_head, int64_t ve, const pr_config& c, int grid, int gmax, int slots,
+                       int loads, int64_t* stat, int64_t* tile_vec) {
+    *stat = 0;
+    *tile_vec = 0;
+    const int64_t nvec = nafter_head / ve;
+    if (nvec * c.vec_bytes < kTailMinBytes) return;
+    const int64_t step = (int64_t)c.unroll * grid * c.block;
+    const int64_t tv = kTileBytes / c.vec_bytes;
+    const int64_t tail = nvec / 10;
+    // the kernel's tile: whole rounds of block x `loads` vectors, as many as
+    // fit in tv (at least one).  Keep the tile count within the gmax slots
+    // and within the blocks' shared partial slots (`slots` a block: every
+    // claimed tile is then reduced, since a block stops claiming only with
+    // its slots full)
+    const int64_t round_vec = (int64_t)c.block * loads;
+    const int64_t tile = tv > round_vec ? tv / round_vec * round_vec : round_vec;
+    const int64_t max_tiles = gmax < (int64_t)grid * slots ? gmax : (int64_t)grid * slots;
+    int64_t s = (nvec - tail) / step * step;
+    while (s < nvec && (nvec - s + tile - 1) / tile > max_tiles) s += step;
+    if (s <= 0 || s >= nvec) return;
+    *stat = s;
+    *tile_vec = tv;
+}
+
 // Persistent grid: SMs x blocks-per-SM (clamped to what is resident at once).
 static pr_status persistent_grid(const KernelEntry* e, const pr_config& c, int sms, int gmax, int* grid) {
     int occ = 0;
@@ -316,9 +372,18 @@ static pr_status persistent_grid(const KernelEntry* e, const pr_config& c, int s
 // Internal launches with an explicit configuration
 // ------------------------------------------------------------------------
 
-static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int prec, bool out_f64, void* out,
-                            void* part_out, cudaStream_t st, const pr_config& cfg, int aux = AUX_NONE,
-                            int64_t* argidx = nullptr) {
+// The launch a plain reduction makes: kernel (grid-stride or claimed tail),
+// shape and arguments.
+struct ReducePlan {
+    const KernelEntry* run = nullptr;
+    pr_config c{};
+    int grid = 0;
+    ReduceArgs a{};
+};
+
+static pr_status plan_reduce(const void* x, int64_t n, int dtype, int op, int prec, bool out_f64, void* out,
+                             void* part_out, cudaStream_t st, const pr_config& cfg, int aux, int64_t* argidx,
+                             ReducePlan* pl) {
     const KernelEntry* e = reg_find(KernelKey{K_REDUCE, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec, (uint8_t)aux,
                                               (uint8_t)cfg.unroll, (uint8_t)cfg.vec_bytes});
     if (!e) return fail(PR_ERR_UNSUPPORTED, "no reduce kernel for dtype %d op %d precision %d", dtype, op, prec);
@@ -341,8 +406,41 @@ static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int pre
     int64_t head = (int64_t)(((uintptr_t)c.vec_bytes - addr % (uintptr_t)c.vec_bytes) % (uintptr_t)c.vec_bytes) / es;
     if (head > n) head = n;
     ReduceArgs a{x, n, head, out, part_out, out_f64 ? 1 : 0, ws, argidx};
+    // large inputs: the claimed-tail variant, where it keeps the same
+    // resident blocks and spills at most a few words more than the
+    // grid-stride kernel (its tile loads take registers)
+    const KernelEntry* run = e;
+    if ((n - head) * es >= kTailMinBytes) {
+        const KernelEntry* et = reg_find(KernelKey{K_REDUCE_TAIL, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec,
+                                                   (uint8_t)aux, (uint8_t)c.unroll, (uint8_t)c.vec_bytes});
+        int occ_s = 0, occ_t = 0;
+        if (et) {
+            s = occupancy(e->fn, c.block, &occ_s);
+            if (s == PR_OK) s = occupancy(et->fn, c.block, &occ_t);
+            if (s != PR_OK) return s;
+        }
+        const int want = c.blocks_per_sm < occ_s ? c.blocks_per_sm : occ_s;
+        if (et && occ_t >= want && local_bytes(et->fn) <= local_bytes(e->fn) + kTailSpillSlack &&
+            (int64_t)c.block * et->tile_loads * c.vec_bytes >= kTailMinRound) {
+            tail_split(n - head, ve, c, grid, ws.gmax, et->tile_slots, et->tile_loads, &a.stat, &a.tile_vec);
+            if (a.tile_vec > 0) run = et;
+        }
+    }
+    pl->run = run;
+    pl->c = c;
+    pl->grid = grid;
+    pl->a = a;
+    return PR_OK;
+}
+
+static pr_status run_reduce(const void* x, int64_t n, int dtype, int op, int prec, bool out_f64, void* out,
+                            void* part_out, cudaStream_t st, const pr_config& cfg, int aux = AUX_NONE,
+                            int64_t* argidx = nullptr) {
+    ReducePlan pl;
+    pr_status s = plan_reduce(x, n, dtype, op, prec, out_f64, out, part_out, st, cfg, aux, argidx, &pl);
+    if (s != PR_OK) return s;
     PR_INJECT_LAUNCH();
-    cudaError_t err = reinterpret_cast<ReduceLaunch>(e->launch)(a, grid, c.block, st);
+    cudaError_t err = reinterpret_cast<ReduceLaunch>(pl.run->launch)(pl.a, pl.grid, pl.c.block, st);
     if (err != cudaSuccess) return fail(PR_ERR_CUDA, "reduce launch: %s", cudaGetErrorString(err));
     return PR_OK;
 }
@@ -1068,6 +1166,32 @@ pr_status pr_debug_inject_fault(int32_t site, int32_t after, int32_t* pending) {
     if (pending) *pending = g_fault_site.load() != PR_FAULT_NONE;
     g_fault_after = after;
     g_fault_site.store(site);
+    return PR_OK;
+}
+
+pr_status pr_debug_reduce_plan(const void* x, int64_t n, pr_dtype dtype, pr_op op, pr_precision precision,
+                               int32_t arg, pr_stream_t stream, int32_t* grid, int32_t* block,
+                               int64_t* tail_vectors) {
+    g_msg.clear();
+    pr_status s = check_common(dtype, op, arg ? PR_PREC_PLAIN : precision);
+    if (s != PR_OK) return s;
+    if (arg && op != PR_MAX && op != PR_MIN) return fail(PR_ERR_UNSUPPORTED, "arg-extremum needs MAX or MIN");
+    if (n < 0) return fail(PR_ERR_INVALID, "n must be >= 0 (got %lld)", (long long)n);
+    if (!x && n > 0) return fail(PR_ERR_INVALID, "x is NULL");
+    if ((s = check_aligned(x, dtype, "x")) != PR_OK) return s;
+    ensure_registered();
+    const int prec = arg ? PR_PREC_PLAIN : precision;
+    const pr_config c = arg ? default_cfg(PR_KIND_REDUCE, dtype, op, prec) : lookup_cfg(PR_KIND_REDUCE, dtype, op, prec, n);
+    ReducePlan pl;
+    s = plan_reduce(x, n, dtype, op, prec, false, nullptr, nullptr, (cudaStream_t)stream, c,
+                    arg ? AUX_ARG : AUX_NONE, nullptr, &pl);
+    if (s != PR_OK) return s;
+    if (grid) *grid = pl.grid;
+    if (block) *block = pl.c.block;
+    if (tail_vectors) {
+        const int64_t ve = pl.c.vec_bytes / elem_size(dtype);
+        *tail_vectors = pl.a.tile_vec > 0 ? (n - pl.a.head) / ve - pl.a.stat : 0;
+    }
     return PR_OK;
 }
 

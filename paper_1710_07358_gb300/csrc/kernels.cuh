@@ -9,9 +9,19 @@
 //     outside [x, x+n); the identity is never needed as a load mask).
 //   Step 3: the U accumulators are combined, then the warp (shuffle butterfly
 //     or redux.sync), then the block (one value per warp in shared memory).
+//   Large inputs (dyn): the grid-stride part stops at a multiple of the
+//     grid's stride near nine tenths of the vectors, and the rest is cut into
+//     tiles of blockDim x TL vectors that blocks claim from an atomic counter
+//     (the next claim issued while the current tile loads).  SMs stream at
+//     unequal rates (their finishing times spread over a few microseconds),
+//     so a static split ends when the slowest SM does; claimed tiles let the
+//     fast SMs take the slow ones' share of the end.  Each tile is reduced by
+//     its block like a block partial and stored in a slot indexed by the
+//     tile, so the result does not depend on which block took which tile.
 //   Stage 2 (Section 2.3), fused: every block stores its partial; the last
 //     block to finish (atomic ticket after a fence) combines all partials in
-//     block-index order, writes the result and re-arms the ticket counter.
+//     block-index order, then the tile partials in tile order, writes the
+//     result and re-arms the ticket and claim counters.
 //
 // k_segmented  many reductions (segments of a CSR offsets array, or equal rows)
 //   in one launch.  The element range [offsets[0], offsets[nseg]) is cut into
@@ -52,11 +62,11 @@ enum : int { kErrInvalid = 1, kErrTimeout = 4 };
 
 struct Workspace {
     char* partials;      // gmax slots (k_reduce)
-    char* head;          // gmax slots (k_segmented: first-segment partial of a block)
+    char* head;          // gmax slots (k_segmented: first-segment partial of a block; k_reduce: tile partials)
     char* tail;          // gmax slots (k_segmented: last-segment partial of a block)
     unsigned* seg_cnt;   // gmax tickets (k_segmented), zero between launches
     unsigned* counter;   // 1 ticket (k_reduce), zero between launches
-    unsigned* chunk_ctr; // next chunk to claim (k_segmented), zero between launches
+    unsigned* chunk_ctr; // next chunk (k_segmented) or tile (k_reduce) to claim, zero between launches
     unsigned* blk_done;  // blocks finished (k_segmented), zero between launches
     int* err;            // device error word
     int gmax;
@@ -71,6 +81,10 @@ struct ReduceArgs {
     int out_f64;
     Workspace ws;
     int64_t* argidx;     // arg-extremum traits: index of the first extremum (may be null)
+    int64_t stat = 0;      // tile_vec > 0: vectors (after the head) of the grid-stride part,
+                           // a multiple of U x threads
+    int64_t tile_vec = 0;  // > 0: the vectors past `stat` are claimed in tiles of about this
+                           // many vectors (partials in ws.head); 0: no claimed tail
 };
 
 struct SegArgs {
@@ -149,6 +163,41 @@ struct MinBlocks<T, std::void_t<decltype(T::kMinBlocks)>> {
     static constexpr int value = T::kMinBlocks;
 };
 
+// A trait whose combine is exact and independent of order (integer,
+// bitwise, max / min and arg-extremum) declares kExact: claimed tail tiles
+// then join its running accumulators, with no partial per tile.
+template <class T, class = void>
+struct Exact {
+    static constexpr bool value = false;
+};
+template <class T>
+struct Exact<T, std::void_t<decltype(T::kExact)>> {
+    static constexpr bool value = T::kExact;
+};
+
+// Vectors a thread loads per round of a claimed tile: four for a float trait
+// whose accumulator is one or two words and whose registers are not capped,
+// U otherwise (exact traits add tiles to their running accumulators).
+template <class T, int U, class = void>
+struct TileLoads {
+    static constexpr int value =
+        (!Exact<T>::value && MinBlocks<T>::value == 1 && sizeof(typename T::Acc) <= 8 && U < 4) ? 4 : U;
+};
+template <class T, int U>
+struct TileLoads<T, U, std::void_t<decltype(T::kTileLoads)>> {   // a trait's own choice
+    static constexpr int value = T::kTileLoads;
+};
+
+// Claimed tail tiles a block of k_reduce holds partials for: one value per
+// warp and tile in shared memory, up to 16 KiB (64 tiles of fp32 partials).
+// Exact traits keep no tile partials.
+template <class T>
+struct TileSlots {
+    static constexpr int kBytes = (MaxBlock<T>::value / 32) * (int)sizeof(typename T::Part);
+    static constexpr int value = Exact<T>::value ? (1 << 20)
+                               : (16384 / kBytes > 64 ? 64 : (16384 / kBytes < 4 ? 4 : 16384 / kBytes));
+};
+
 template <class T>
 __device__ __forceinline__ typename T::Part* slot(char* base, int64_t i) {
     return reinterpret_cast<typename T::Part*>(base + i * kSlot);
@@ -167,7 +216,7 @@ __device__ __forceinline__ typename T::Part fold(typename T::Acc (&acc)[U]) {
 // Plain reduction
 // ------------------------------------------------------------------------
 
-template <class T, int U, int VB>
+template <class T, int U, int VB, bool TAIL>
 __device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
     using Ld = typename T::Ld;
     using In = typename Ld::In;
@@ -184,13 +233,35 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t head = a.head;
     const int64_t nvec = (a.n - head) / VE;
+    const bool dyn = TAIL && a.tile_vec > 0;
+    int64_t nstat = nvec;                           // vectors of the grid-stride part
+    if constexpr (TAIL) nstat = dyn ? a.stat : nvec;
     const char* xv = reinterpret_cast<const char*>(x + head);
+    using GR = GridR<T>;
+    using G = typename GR::Part;
+    // claimed tiles: thread 0 makes the block's first two claims while the
+    // loads of its last grid-stride step travel (claims made earlier would
+    // hand out tiles by start order rather than by progress), keeps them in
+    // shared memory, and then at each tile publishes the claim it made a
+    // tile earlier and makes the next, so no warp waits for a claim's round
+    // trip
+    __shared__ unsigned s_claim[2], s_claim1;
+    bool claimed = false;
+    auto claim_first = [&]() {
+        if constexpr (TAIL)
+            if (dyn && !claimed && threadIdx.x == 0) {
+                s_claim[0] = atomicAdd(a.ws.chunk_ctr, 1u);
+                s_claim1 = atomicAdd(a.ws.chunk_ctr, 1u);
+                claimed = true;
+            }
+    };
 
     int64_t i = tid;
-    for (; i + (int64_t)(U - 1) * nth < nvec; i += (int64_t)U * nth) {
+    for (; i + (int64_t)(U - 1) * nth < nstat; i += (int64_t)U * nth) {
         Words<VB> w[U];
 #pragma unroll
         for (int u = 0; u < U; u++) w[u] = ldv<VB>(xv + (i + u * nth) * VB);
+        if (i + (int64_t)(2 * U - 1) * nth >= nstat) claim_first();   // the last step
 #pragma unroll
         for (int u = 0; u < U; u++) {
             E e[VE];
@@ -198,7 +269,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
             T::add_vec(acc[u], e, head + (i + u * nth) * VE);
         }
     }
-    for (; i < nvec; i += nth) {
+    for (; i < nstat; i += nth) {
         Words<VB> w = ldv<VB>(xv + i * VB);
         E e[VE];
         Ld::template dec<VB>(w, e);
@@ -206,13 +277,115 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
     }
     if (tid < head) T::add(acc[0], Ld::one(x, tid), tid);
     for (int64_t j = head + nvec * VE + tid; j < a.n; j += nth) T::add(acc[0], Ld::one(x, j), j);
+    claim_first();   // (a grid-stride part too short for the loop)
+    unsigned c_next = ~0u;
 
-    using GR = GridR<T>;
-    using G = typename GR::Part;
+    // claimed tiles: vectors [nstat, nvec) in tiles of R rounds of blockDim x
+    // TL vectors (R from the requested tile size), the next claim issued with
+    // a tile's first loads.  An exact trait adds them to its accumulators
+    // (each still sees its vectors in increasing index order: tiles lie past
+    // the grid-stride part and a block's claims increase), with U loads a
+    // thread.  Any other trait reduces each tile like a block partial into a
+    // slot indexed by the tile, with four loads a thread where its
+    // accumulator is one or two words and its registers are not capped (U
+    // where four would spill).
+    constexpr bool EX = Exact<T>::value;
+    constexpr int TL = TileLoads<T, U>::value;
+    const int64_t round_vec = (int64_t)blockDim.x * TL;
+    const int rounds = dyn && a.tile_vec > round_vec ? (int)(a.tile_vec / round_vec) : 1;
+    const int64_t tile = round_vec * rounds;
+    const int64_t ntiles = dyn ? (nvec - nstat + tile - 1) / tile : 0;
+    // one tile into accumulators ac; with its first loads thread 0 publishes
+    // the next tile (claimed a tile earlier) and claims the one after (if
+    // `more`: a block of a float trait stops claiming when its TileSlots
+    // partial slots are full)
+    auto run_tile = [&](typename T::Acc (&ac)[U], unsigned t, int k, bool more) {
+        const int64_t v0 = nstat + (int64_t)t * tile + threadIdx.x;   // this thread's first vector
+        const char* p0 = xv + v0 * VB;
+        const int64_t left = nvec - v0;                               // vectors from v0 to the end
+        const bool full = left >= tile;                               // every tile but the last
+        for (int r = 0; r < rounds; r++) {
+            const int64_t o = (int64_t)r * round_vec;
+            Words<VB> w[TL];
+#pragma unroll
+            for (int q = 0; q < TL; q++)
+                if (full || o + q * (int)blockDim.x < left) w[q] = ldv<VB>(p0 + (o + q * (int)blockDim.x) * VB);
+            if (r == 0 && threadIdx.x == 0) {
+                s_claim[(k + 1) & 1] = c_next;
+                c_next = more ? atomicAdd(a.ws.chunk_ctr, 1u) : ~0u;
+            }
+#pragma unroll
+            for (int q = 0; q < TL; q++) {
+                const int64_t oq = o + q * (int)blockDim.x;
+                if (full || oq < left) {
+                    E e[VE];
+                    Ld::template dec<VB>(w[q], e);
+                    T::add_vec(ac[q % U], e, head + (v0 + oq) * VE);
+                }
+            }
+        }
+    };
+    if constexpr (TAIL && EX) {
+        if (dyn) {
+            __syncthreads();   // the first claims, in shared memory
+            unsigned t = s_claim[0];
+            if (threadIdx.x == 0) c_next = s_claim1;
+            for (int k = 0; (int64_t)t < ntiles; k++) {
+                run_tile(acc, t, k, true);
+                __syncthreads();
+                t = s_claim[(k + 1) & 1];
+            }
+        }
+    }
+
     const Part p = block_combine<T>(fold<T, U>(acc));
 
+    int ktiles = 0;   // tiles this block reduced (float traits)
+    if constexpr (TAIL && !EX) if (dyn) {
+        // a tile's partial: each warp's value in a shared slot (no combine
+        // across warps inside the loop, so no warp falls behind the others
+        // between barriers); after the block's last tile, thread j combines
+        // its tile j's warp values in warp order and stores them in the
+        // tile's slot
+        constexpr int NW = MaxBlock<T>::value / 32;
+        constexpr int NS = TileSlots<T>::value;
+        __shared__ Part s_tp[NS][NW];
+        __shared__ unsigned s_tid[NS];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int nwarps = (blockDim.x + 31) >> 5;
+        unsigned t = s_claim[0];   // written before block_combine's barriers
+        if (threadIdx.x == 0) c_next = s_claim1;
+        int k = 0;
+        while ((int64_t)t < ntiles) {
+            typename T::Acc ta[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) ta[u] = T::init();
+            run_tile(ta, t, k, k + 2 < NS);
+            const Part tp = T::warp_reduce(fold<T, U>(ta));
+            if (lane == 0) s_tp[k][warp] = tp;
+            if (threadIdx.x == 0) s_tid[k] = t;
+            __syncthreads();
+            t = s_claim[(k + 1) & 1];
+            k++;
+        }
+        if ((int)threadIdx.x < k) {
+            Part q = s_tp[threadIdx.x][0];
+            for (int w = 1; w < nwarps; w++) q = T::combine(q, s_tp[threadIdx.x][w]);
+            *slot<GR>(a.ws.head, s_tid[threadIdx.x]) = GR::up(q);
+        }
+        ktiles = k;
+    }
+
+    // every thread that wrote a partial (thread 0 the block's, and with a
+    // claimed tail of a float trait the first threads their tiles') fences;
+    // a barrier then orders those writes before thread 0's ticket
     __shared__ unsigned s_last;
-    if (threadIdx.x == 0) {
+    if constexpr (TAIL && !EX) {
+        if (threadIdx.x == 0) *slot<GR>(a.ws.partials, blockIdx.x) = GR::up(p);
+        if (threadIdx.x == 0 || (int)threadIdx.x < ktiles) __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = (atomicAdd(a.ws.counter, 1u) == gridDim.x - 1);
+    } else if (threadIdx.x == 0) {
         *slot<GR>(a.ws.partials, blockIdx.x) = GR::up(p);
         __threadfence();
         const unsigned ticket = atomicAdd(a.ws.counter, 1u);
@@ -222,7 +395,25 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
     if (!s_last) return;
     __threadfence();
     G q = GR::part_init();
-    for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) q = GR::combine(q, ld_cg_any(slot<GR>(a.ws.partials, j)));
+    if constexpr (TAIL && !EX) {
+        // block partials, then tile partials in tile order; the tile loop is
+        // unrolled so that a thread's loads of several slots travel together
+        for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x)
+            q = GR::combine(q, ld_cg_any(slot<GR>(a.ws.partials, j)));
+        const int nt = (int)ntiles;
+        int j = threadIdx.x;
+        for (; j + 3 * (int)blockDim.x < nt; j += 4 * blockDim.x) {
+            G v[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) v[r] = ld_cg_any(slot<GR>(a.ws.head, j + r * (int)blockDim.x));
+#pragma unroll
+            for (int r = 0; r < 4; r++) q = GR::combine(q, v[r]);
+        }
+        for (; j < nt; j += blockDim.x) q = GR::combine(q, ld_cg_any(slot<GR>(a.ws.head, j)));
+    } else {
+        for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x)
+            q = GR::combine(q, ld_cg_any(slot<GR>(a.ws.partials, j)));
+    }
     q = block_combine<GR>(q);
     if (threadIdx.x == 0) {
         if (a.part_out) {
@@ -232,6 +423,8 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
             GR::store_aux(a.argidx, nullptr, 0, q, 0);
         }
         *a.ws.counter = 0u;
+        if constexpr (TAIL)
+            if (dyn) *a.ws.chunk_ctr = 0u;
     }
 }
 
@@ -240,18 +433,20 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
 // bound, with which the compiler chooses their registers freely (an explicit
 // minimum of one block makes it take more, and so halves some traits'
 // occupancy).
-template <class T, int U, int VB>
+// TAIL: the variant with claimed tail tiles (large inputs; its tile loads
+// take registers the grid-stride kernel does not need).
+template <class T, int U, int VB, bool TAIL>
 __global__ void __launch_bounds__(MaxBlock<T>::value) k_reduce(ReduceArgs a) {
-    reduce_body<T, U, VB>(a);
+    reduce_body<T, U, VB, TAIL>(a);
 }
-template <class T, int U, int VB>
+template <class T, int U, int VB, bool TAIL>
 __global__ void __launch_bounds__(MaxBlock<T>::value, MinBlocks<T>::value) k_reduce_occ(ReduceArgs a) {
-    reduce_body<T, U, VB>(a);
+    reduce_body<T, U, VB, TAIL>(a);
 }
-template <class T, int U, int VB>
+template <class T, int U, int VB, bool TAIL = false>
 constexpr auto reduce_kernel() {
-    if constexpr (MinBlocks<T>::value > 1) return &k_reduce_occ<T, U, VB>;
-    else return &k_reduce<T, U, VB>;
+    if constexpr (MinBlocks<T>::value > 1) return &k_reduce_occ<T, U, VB, TAIL>;
+    else return &k_reduce<T, U, VB, TAIL>;
 }
 
 // One block: out = parts[0] (x) parts[1] (x) ... in index order (slot stride kSlot).

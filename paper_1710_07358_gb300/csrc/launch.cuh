@@ -6,9 +6,9 @@
 
 namespace pr {
 
-template <class T, int U, int VB>
+template <class T, int U, int VB, bool TAIL>
 cudaError_t launch_reduce(const ReduceArgs& a, int grid, int block, cudaStream_t st) {
-    reduce_kernel<T, U, VB>()<<<grid, block, 0, st>>>(a);
+    reduce_kernel<T, U, VB, TAIL>()<<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -52,8 +52,13 @@ template <class T, int U, int VB>
 void reg_one(uint8_t dtype, uint8_t op, uint8_t prec, uint8_t aux, bool plain, bool seg) {
     if (plain) {
         reg_add(KernelKey{K_REDUCE, dtype, op, prec, aux, (uint8_t)U, (uint8_t)VB},
-                KernelEntry{reinterpret_cast<const void*>(reduce_kernel<T, U, VB>()),
-                            reinterpret_cast<void*>(&launch_reduce<T, U, VB>)});
+                KernelEntry{reinterpret_cast<const void*>(reduce_kernel<T, U, VB, false>()),
+                            reinterpret_cast<void*>(&launch_reduce<T, U, VB, false>)});
+        KernelEntry et{reinterpret_cast<const void*>(reduce_kernel<T, U, VB, true>()),
+                       reinterpret_cast<void*>(&launch_reduce<T, U, VB, true>)};
+        et.tile_slots = TileSlots<T>::value;
+        et.tile_loads = TileLoads<T, U>::value;
+        reg_add(KernelKey{K_REDUCE_TAIL, dtype, op, prec, aux, (uint8_t)U, (uint8_t)VB}, et);
     }
     if (seg) {
         reg_add(KernelKey{K_SEGMENTED, dtype, op, prec, aux, (uint8_t)U, (uint8_t)VB},

@@ -18,7 +18,8 @@ struct BwdArgs;
 
 enum Kind : uint8_t {
     K_REDUCE = 0, K_SEGMENTED = 1, K_BACKWARD = 2, K_COMBINE = 3, K_ROWS = 4,
-    K_AXIS = 5, K_AXIS_FINISH = 6, K_AXIS_EMPTY = 7, K_AXIS_BACKWARD = 8, K_SCAN = 9
+    K_AXIS = 5, K_AXIS_FINISH = 6, K_AXIS_EMPTY = 7, K_AXIS_BACKWARD = 8, K_SCAN = 9,
+    K_REDUCE_TAIL = 10  // k_reduce with claimed tail tiles (large inputs)
 };
 enum Aux : uint8_t { AUX_NONE = 0, AUX_ARG = 1, AUX_PROD = 2 };
 
@@ -40,6 +41,8 @@ struct KernelEntry {
     const void* fn;      // the __global__ function (occupancy queries)
     void* launch;        // one of the *Launch types above, by kind
     int part_bytes = 0;  // K_AXIS: bytes of one cross-warp partial
+    int tile_slots = 0;  // K_REDUCE_TAIL: claimed tiles a block holds partials for
+    int tile_loads = 0;  // K_REDUCE_TAIL: vectors a thread loads per round of a tile
 };
 
 void reg_add(const KernelKey& k, const KernelEntry& e);

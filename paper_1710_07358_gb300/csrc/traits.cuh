@@ -293,6 +293,7 @@ struct IntOp {
     using Acc = AccT;   // uint32_t, or uint64_t (int32 sum widened, int64)
     using Part = AccT;
     static constexpr bool kIdx = false;
+    static constexpr bool kExact = true;   // combine exact and order free
     __device__ __forceinline__ static AccT ident() {
         return OpK == 1 ? (AccT)1 : (OpK == 4 ? (AccT)~(AccT)0 : (AccT)0);
     }
@@ -439,6 +440,7 @@ struct MaxMin {
     using Acc = K;
     using Part = K;
     static constexpr bool kIdx = false;
+    static constexpr bool kExact = true;   // combine exact and order free
     __device__ __forceinline__ static K pick(K a, K b) { return MX ? (a > b ? a : b) : (a < b ? a : b); }
     __device__ __forceinline__ static Acc init() { return Key::ident(MX); }
     template <int N>
@@ -483,6 +485,7 @@ struct MaxMinF {
     using Acc = float;
     using Part = uint32_t;
     static constexpr bool kIdx = false;
+    static constexpr bool kExact = true;   // combine exact and order free
     __device__ __forceinline__ static float f(float a, float b) {
         float r;
         if (MX) asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
@@ -527,6 +530,7 @@ struct ArgExt {
     struct Acc { K key; int64_t idx; };
     using Part = Acc;
     static constexpr bool kIdx = true;
+    static constexpr bool kExact = true;   // combine exact and order free
     static constexpr int64_t kNone = INT64_MAX;
     __device__ __forceinline__ static bool better(K ka, int64_t ia, K kb, int64_t ib) {
         return (MX ? ka > kb : ka < kb) || (ka == kb && ia < ib);
@@ -583,6 +587,7 @@ struct ArgExtF {
     using Base = ArgExt<Key, MX>;
     using Part = typename Base::Part;
     static constexpr bool kIdx = true;
+    static constexpr bool kExact = true;   // combine exact and order free
     static constexpr int kMaxN = 32 / Ld::ES;     // elements of the widest vector
     static constexpr int kMaxBlock = 512;         // the saved vectors need up to 128 registers
     struct Acc {

@@ -67,6 +67,8 @@ _SIGS = {
     "pr_reduce_noalloc": [_P, _I64, _I, _I, _P, _P],
     "pr_prepare": [_P],
     "pr_debug_inject_fault": [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_I32)],
+    "pr_debug_reduce_plan": [_P, _I64, _I, _I, _I, _I32, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                             ctypes.POINTER(_I64)],
     "pr_last_device_error": [_P, ctypes.POINTER(_I32)],
     "pr_get_config": [_I, _I, _I, _I, _I64, ctypes.POINTER(pr_config)],
     "pr_set_config": [_I, _I, _I, _I, _I64, ctypes.POINTER(pr_config)],
@@ -200,6 +202,21 @@ def inject_fault(site: str, after: int = 0) -> bool:
     p = ctypes.c_int32(0)
     check(pr_debug_inject_fault(FAULT_SITES[site], after, ctypes.byref(p)))
     return bool(p.value)
+
+
+def pr_debug_reduce_plan(x, n, dtype, op, precision, arg, stream, grid_ref, block_ref, tail_ref):
+    return lib().pr_debug_reduce_plan(x, n, dtype, op, precision, arg, stream, grid_ref, block_ref, tail_ref)
+
+
+def reduce_plan(x, op: str, precision: str = "plain", arg: bool = False, stream=None) -> dict:
+    """The launch reduce() (or reduce_arg(), with arg) would make for x:
+    {"grid", "block", "tail_vectors"} (tail_vectors: the vectors past the
+    grid-stride part that blocks claim in tiles; 0 for none)."""
+    g, b, t = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+    check(pr_debug_reduce_plan(_ptr(x), x.numel(), DTYPES[dtype_name(x)], OPS[op], PRECISIONS[precision],
+                               1 if arg else 0, _stream(x, stream), ctypes.byref(g), ctypes.byref(b),
+                               ctypes.byref(t)))
+    return {"grid": g.value, "block": b.value, "tail_vectors": t.value}
 
 
 def pr_last_device_error(stream, code_ref):

@@ -245,3 +245,15 @@ def test_fault_hook_arguments_and_validation_order(L):
         assert pr.pr_line_search(FAKE, FAKE, FAKE, FAKE, 100, 0.15, 4, 1.0, 1.0, 0, 10, 2, FAKE, None) == INVALID
         assert pr.inject_fault("none") is True            # still armed: nothing consumed it
         assert pr.inject_fault("none") is False
+
+
+def test_reduce_plan_rejects(L):
+    """The launch-plan query validates like the reductions it describes, on the
+    host, before it touches a device."""
+    g, b, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    refs = (ctypes.byref(g), ctypes.byref(b), ctypes.byref(t))
+    assert pr.pr_debug_reduce_plan(FAKE, -1, F32, SUM, 0, 0, None, *refs) == INVALID
+    assert pr.pr_debug_reduce_plan(None, 4, F32, SUM, 0, 0, None, *refs) == INVALID
+    assert pr.pr_debug_reduce_plan(FAKE, 4, 99, SUM, 0, 0, None, *refs) == INVALID
+    assert pr.pr_debug_reduce_plan(FAKE, 4, F32, SUM, 0, 1, None, *refs) == UNSUPPORTED   # arg needs MAX / MIN
+    assert pr.pr_debug_reduce_plan(FAKE, 4, F32, 4, 0, 0, None, *refs) == UNSUPPORTED     # AND on floats
