@@ -909,11 +909,14 @@ def run_ours(args):
 
     achieved = gbs(nbytes, per_launch)
     cfg = pr.get_config("reduce", "f32", "sum", "plain", N_HEAD)
+    plan = pr.reduce_plan(x, "sum")
     traffic = traffic_for("reduce_f32_sum_2^28")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy)",
-                "kernel": "k_reduce<SumF<LdF32,float>,U=%d,VB=%d>" % (cfg["unroll"], cfg["vec_bytes"]),
+                "kernel": "k_reduce<SumF<LdF32,float>,U=%d,VB=%d,TAIL=%d>" % (
+                    cfg["unroll"], cfg["vec_bytes"], 1 if plan["tail_vectors"] else 0),
+                "claimed_tail_vectors": plan["tail_vectors"],
                 "algorithmic_bytes_per_launch": nbytes, "launch_us": round(per_launch * 1e3, 2)}
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
