@@ -243,15 +243,14 @@ __global__ void __launch_bounds__(kPhiThreads, MP <= 8 ? 2 : 1) k_phi(PhiArgs a)
 
 // F_0 = F_1 = 1, F_k = F_{k-1} + F_{k-2} by float64 additions: exact up to
 // F_77; F_78 (above 2^53) is the IEEE rounding of the exact sum, as in any
-// float64 evaluation of the same recurrence
-__device__ double fib(int k) {
-    double a = 1.0, b = 1.0;
-    for (int i = 1; i < k; i++) {
-        const double t = __dadd_rn(a, b);
-        a = b;
-        b = t;
-    }
-    return b;
+// float64 evaluation of the same recurrence.  k_ls_init fills the search
+// state's table once; the search step reads it (a step that ran the
+// recurrence for each point it placed spent about 4 us a pass in the chain
+// of dependent float64 additions).
+__device__ void fill_fib(double* f) {
+    f[0] = 1.0;
+    f[1] = 1.0;
+    for (int k = 2; k <= kLsMaxFib; k++) f[k] = __dadd_rn(f[k - 1], f[k - 2]);
 }
 
 struct LsNode {
@@ -282,12 +281,12 @@ __device__ double ls_child(const LsState& s, const LsNode& n, int br, LsNode& c)
     if (br == 0) {
         c.b = n.x2;
         c.x2 = n.x1;
-        c.x1 = last ? __dsub_rn(c.x2, __dmul_rn(0.1, s.u)) : __dadd_rn(c.a, __dmul_rn(fib(N - j - 2), s.u));
+        c.x1 = last ? __dsub_rn(c.x2, __dmul_rn(0.1, s.u)) : __dadd_rn(c.a, __dmul_rn(s.fib[N - j - 2], s.u));
         return c.x1;
     }
     c.a = n.x1;
     c.x1 = n.x2;
-    c.x2 = last ? __dadd_rn(c.x1, __dmul_rn(0.1, s.u)) : __dadd_rn(c.a, __dmul_rn(fib(N - j - 1), s.u));
+    c.x2 = last ? __dadd_rn(c.x1, __dmul_rn(0.1, s.u)) : __dadd_rn(c.a, __dmul_rn(s.fib[N - j - 1], s.u));
     return c.x2;
 }
 
@@ -324,9 +323,10 @@ __global__ void k_ls_init(LsState* sp, double lo, double hi, int method, int cou
         s.x1 = __dsub_rn(hi, __dmul_rn(s.golden, __dsub_rn(hi, lo)));
         s.x2 = __dadd_rn(lo, __dmul_rn(s.golden, __dsub_rn(hi, lo)));
     } else {
-        s.u = __ddiv_rn(__dsub_rn(hi, lo), fib(count));
-        s.x1 = __dadd_rn(lo, __dmul_rn(fib(count - 2), s.u));
-        s.x2 = __dadd_rn(lo, __dmul_rn(fib(count - 1), s.u));
+        fill_fib(s.fib);
+        s.u = __ddiv_rn(__dsub_rn(hi, lo), s.fib[count]);
+        s.x1 = __dadd_rn(lo, __dmul_rn(s.fib[count - 2], s.u));
+        s.x2 = __dadd_rn(lo, __dmul_rn(s.fib[count - 1], s.u));
     }
     s.pts[0] = s.x1;
     s.pts[1] = s.x2;

@@ -8,6 +8,7 @@
 namespace pr {
 
 constexpr int kLsMaxDepth = 3;                       // iterations decided per pass, at most
+constexpr int kLsMaxFib = 78;                        // Fibonacci search: at most 78 evaluations
 constexpr int kLsMaxPts = 2 + (2 << kLsMaxDepth) - 2; // first pass: 2 initial points + the tree
 constexpr int kPhiThreads = 256;
 
@@ -22,6 +23,7 @@ struct LsState {
     double golden;     // (sqrt(5) - 1) / 2
     double pts[kLsMaxPts];
     double vals[kLsMaxPts];
+    double fib[kLsMaxFib + 1];   // F_0 .. F_78 (F_0 = F_1 = 1), filled by k_ls_init
     int32_t method;    // 0 golden-section, 1 Fibonacci
     int32_t count;     // golden: iterations; Fibonacci: evaluations N
     int32_t iter, total, depth, first, npts, done;
