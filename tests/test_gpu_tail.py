@@ -194,6 +194,11 @@ def test_compensated_and_product_forms_with_the_tail(shape, inputs):
     assert oracle.sum_error(x, "f32", got) <= sum_bound(x, "f32", "compensated")
     r64 = values_of(pr.reduce(t, "sum", precision="compensated", out_dtype="f64"), "f64")[0]
     assert oracle.sum_error(x, "f32", r64) <= sum_bound(x, "f32", "compensated")
+    # fp32 accumulators with the fp64 combine: the tiles' partials are fp64 too
+    shape("f32", "sum", ONE_PER_SM, precision="fp64_combine")
+    assert plan(t, "sum", precision="fp64_combine")["tail_vectors"] > 0
+    got = values_of(pr.reduce(t, "sum", precision="fp64_combine"), "f32")[0]
+    assert oracle.sum_error(x, "f32", got) <= sum_bound(x, "f32", "fp64_combine")
     n64 = (1 << 28) + 9
     xp = synth.uniform_f64(n64, 813)
     tp = to_device(xp, "f64")
@@ -217,3 +222,30 @@ def test_segmented_after_a_tail_reduction_on_the_same_stream(inputs):
     assert all(same_float(a, float(b)) for a, b in zip(got, want))
     again = values_of(pr.reduce(t, "sum"), "f32")[0]
     assert oracle.sum_error(x, "f32", again) <= sum_bound(x, "f32")
+
+
+@pytest.mark.parametrize("launch", ["table", "1024x1"])
+def test_float_product_with_planted_factors_is_exact(launch, shape):
+    """fp32 product of 2^28 + 1237 factors, all 1 except 64 twos and 60
+    halves spread over the grid-stride part and the claimed tiles: every
+    partial product is a power of two within range, so any association gives
+    exactly 16; a zero in the last tile then gives +0."""
+    import torch
+    x = torch.ones(N, dtype=torch.float32, device="cuda")
+    if launch == "1024x1":
+        shape("f32", "prod", ONE_PER_SM)
+        assert plan(x, "prod")["tail_vectors"] > 0
+    ts = tail_start(x, "prod") if plan(x, "prod")["tail_vectors"] > 0 else N - N // 10
+    rng = np.random.default_rng(817)
+    twos = np.concatenate([rng.integers(0, ts, 32), rng.integers(ts, N, 32)])
+    halves = np.concatenate([rng.integers(0, ts, 30), rng.integers(ts, N, 30)])
+    twos = np.unique(twos)
+    halves = np.setdiff1d(np.unique(halves), twos)
+    x[torch.from_numpy(twos).cuda()] = 2.0
+    x[torch.from_numpy(halves).cuda()] = 0.5
+    want = 2.0 ** (len(twos) - len(halves))
+    g = Guarded((), torch.float32)
+    pr.reduce(x, "prod", out=g.tensor)
+    assert values_of(g.check(), "f32")[0] == want
+    x[N - 2] = 0.0
+    assert same_float(values_of(pr.reduce(x, "prod"), "f32")[0], 0.0)
