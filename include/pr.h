@@ -91,6 +91,9 @@ typedef enum {
 } pr_precision;
 
 /* Launch configuration of one kernel family (chosen by the autotuner).
+ * Plain reductions of at most 64 KiB ignore it: they run as one block of
+ * (up to) 1024 threads with two 32-byte vectors a thread, which finishes
+ * without the cross-block ticket.
  *   block          threads per block (multiple of 32, 64..1024)
  *   blocks_per_sm  persistent blocks per SM (clamped to the occupancy limit)
  *   unroll         independent accumulators / vectors in flight per thread (1,2,4,8)

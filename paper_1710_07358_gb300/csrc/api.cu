@@ -381,9 +381,16 @@ struct ReducePlan {
     ReduceArgs a{};
 };
 
+// Inputs of at most kOneBlockBytes run as one block of (up to) 1024 threads
+// with two 32-byte vectors a thread: one step covers them, and a single block
+// finishes without the ticket (measured on GB300, fp32 sum from a CUDA graph:
+// 1024 elements 2.5 -> 1.6 us a call, 8192 elements 2.9 -> 2.0 us).
+constexpr int64_t kOneBlockBytes = (int64_t)64 << 10;
+
 static pr_status plan_reduce(const void* x, int64_t n, int dtype, int op, int prec, bool out_f64, void* out,
-                             void* part_out, cudaStream_t st, const pr_config& cfg, int aux, int64_t* argidx,
+                             void* part_out, cudaStream_t st, const pr_config& cfg_in, int aux, int64_t* argidx,
                              ReducePlan* pl) {
+    const pr_config cfg = n * elem_size(dtype) <= kOneBlockBytes ? pr_config{1024, 1, 2, 32} : cfg_in;
     const KernelEntry* e = reg_find(KernelKey{K_REDUCE, (uint8_t)dtype, (uint8_t)op, (uint8_t)prec, (uint8_t)aux,
                                               (uint8_t)cfg.unroll, (uint8_t)cfg.vec_bytes});
     if (!e) return fail(PR_ERR_UNSUPPORTED, "no reduce kernel for dtype %d op %d precision %d", dtype, op, prec);
@@ -402,6 +409,7 @@ static pr_status plan_reduce(const void* x, int64_t n, int dtype, int op, int pr
     const int64_t per_block = (int64_t)c.block * ve * c.unroll;
     const int64_t need = (n + per_block - 1) / per_block;
     if (need < grid) grid = need < 1 ? 1 : (int)need;
+    if (n * es <= kOneBlockBytes) grid = 1;   // (a kernel built for fewer threads loops twice)
     const uintptr_t addr = reinterpret_cast<uintptr_t>(x);
     int64_t head = (int64_t)(((uintptr_t)c.vec_bytes - addr % (uintptr_t)c.vec_bytes) % (uintptr_t)c.vec_bytes) / es;
     if (head > n) head = n;

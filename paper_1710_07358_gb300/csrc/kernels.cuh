@@ -376,6 +376,27 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
         ktiles = k;
     }
 
+    // the result (valid in thread 0) to out, or as a Part to part_out
+    auto finish = [&](const G& q) {
+        if (a.part_out) {
+            *static_cast<G*>(a.part_out) = q;
+        } else {
+            GR::store(a.out, 0, q, a.out_f64 != 0);
+            GR::store_aux(a.argidx, nullptr, 0, q, 0);
+        }
+    };
+    // one block (small inputs): its partial is the only one, so it finishes
+    // at once, with the same combine the last block would make, and no
+    // round trip through memory, fence or ticket
+    if constexpr (!TAIL) {
+        if (gridDim.x == 1) {
+            G q = threadIdx.x == 0 ? GR::combine(GR::part_init(), GR::up(p)) : GR::part_init();
+            q = block_combine<GR>(q);
+            if (threadIdx.x == 0) finish(q);
+            return;
+        }
+    }
+
     // every thread that wrote a partial (thread 0 the block's, and with a
     // claimed tail of a float trait the first threads their tiles') fences;
     // a barrier then orders those writes before thread 0's ticket
@@ -416,12 +437,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a) {
     }
     q = block_combine<GR>(q);
     if (threadIdx.x == 0) {
-        if (a.part_out) {
-            *static_cast<G*>(a.part_out) = q;
-        } else {
-            GR::store(a.out, 0, q, a.out_f64 != 0);
-            GR::store_aux(a.argidx, nullptr, 0, q, 0);
-        }
+        finish(q);
         *a.ws.counter = 0u;
         if constexpr (TAIL)
             if (dyn) *a.ws.chunk_ctr = 0u;

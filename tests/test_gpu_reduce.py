@@ -294,3 +294,42 @@ def test_reduce_arg_nan_and_signed_zero():
     assert same_float(v.item(), 0.0) and i.item() == 5000
     v, i = pr.reduce_arg(to_device(z, "f32"), "min")
     assert same_float(v.item(), -0.0) and i.item() == 0
+
+
+@pytest.mark.parametrize("dtype,op,precision", [("f32", "sum", "plain"), ("f32", "sum", "compensated"),
+                                                ("f32", "max", "plain"), ("bf16", "sum", "compensated"),
+                                                ("i32", "sum", "plain"), ("u32", "xor", "plain"),
+                                                ("f64", "prod", "plain")])
+@pytest.mark.parametrize("nbytes", [4, 4096, 65536])
+def test_small_inputs_run_as_one_block(dtype, op, precision, nbytes):
+    """Inputs of at most 64 KiB: one block, which finishes without the
+    ticket; results as the oracle's, misaligned too, and the same bits on a
+    repeat.  (One byte more is a multi-block launch.)"""
+    import torch
+    es = {"f32": 4, "bf16": 2, "i32": 4, "u32": 4, "f64": 8}[dtype]
+    n = nbytes // es
+    gen = {"f32": lambda m, s: synth.uniform_f32(m, s), "bf16": synth.normal_bf16, "i32": synth.uniform_i32,
+           "u32": synth.random_u32, "f64": synth.uniform_f64}[dtype]
+    x = gen(n, 60 + n % 7)
+    for offset in (0, 1):
+        t = to_device(x, dtype, offset)
+        assert pr.reduce_plan(t, op, precision=precision)["grid"] == 1
+        od = "f32" if (dtype == "bf16" and op == "sum") else pr.out_dtype_name(dtype, op)
+        got = values_of(pr.reduce(t, op, precision=precision), od)[0]
+        assert values_of(pr.reduce(t, op, precision=precision), od)[0] == got
+        if op == "sum" and dtype in ("f32", "bf16"):
+            assert oracle.sum_error(x, dtype, got) <= sum_bound(x, dtype, precision)
+        elif op == "prod":
+            want = oracle.reduce(x, dtype, op)
+            assert abs(got - want) <= prod_rel_bound(n, dtype) * abs(want)
+        elif dtype == "f32":
+            assert same_float(got, oracle.reduce(x, dtype, op))
+        else:
+            assert got == oracle.reduce(x, dtype, op)
+    if dtype == "f32" and op == "max":
+        v, i = pr.reduce_arg(to_device(x, dtype), "max")
+        assert pr.reduce_plan(to_device(x, dtype), "max", arg=True)["grid"] == 1
+        wv, wi = oracle.argext(x, "f32", "max")
+        assert float(v.item()) == wv and int(i.item()) == wi
+    big = to_device(gen(n + 64 // es + 1, 61), dtype)
+    assert pr.reduce_plan(big, op, precision=precision)["grid"] > 1 or nbytes < 65536
