@@ -641,6 +641,10 @@ static pr_status run_axis(const void* x, int64_t outer, int64_t n, int64_t inner
     int64_t splits = (want + tiles - 1) / tiles;
     if (splits > max_split) splits = max_split;
     if (splits < 1) splits = 1;
+    // a split holds fewer than 2^31 rows (the float arg-extremum keeps its
+    // row as a 32-bit offset within the split)
+    const int64_t kMaxSplitRows = (int64_t)1 << 30;
+    if ((n + splits - 1) / splits > kMaxSplitRows) splits = (n + kMaxSplitRows - 1) / kMaxSplitRows;
     a.rows_per_split = (n + splits - 1) / splits;
     a.splits = (n + a.rows_per_split - 1) / a.rows_per_split;
     if (a.splits > 1) {

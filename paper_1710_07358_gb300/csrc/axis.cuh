@@ -50,6 +50,13 @@ struct HasOrdered : std::false_type {};
 template <class T>
 struct HasOrdered<T, std::void_t<decltype(&T::add_ordered)>> : std::true_type {};
 
+// A trait whose in-order step runs on a caller's (value, row) register pair
+// (kOrderedPair: the arg-extremum of floats).
+template <class T, class = void>
+struct HasOrderedPair : std::false_type {};
+template <class T>
+struct HasOrderedPair<T, std::void_t<decltype(T::kOrderedPair)>> : std::true_type {};
+
 template <class T>
 __device__ __forceinline__ void add_in_order(typename T::Acc& a, typename T::Ld::E v, int64_t i) {
     if constexpr (HasOrdered<T>::value) T::add_ordered(a, v, i);
@@ -94,7 +101,56 @@ __global__ void __launch_bounds__(MaxBlock<T>::value) k_axis(AxisArgs a) {
     Acc acc[VE];
 #pragma unroll
     for (int k = 0; k < VE; k++) acc[k] = T::init();
-    if (has) {
+    if constexpr (HasOrderedPair<T>::value) {
+        // per element the running extremum and its row relative to r0 (a
+        // split holds fewer than 2^31 rows): three operations an element
+        // (pick, compare of bits, select) instead of the accumulator's
+        // 64-bit index and its "none yet" test; started at this lane's first
+        // row, then the same steps as add_ordered
+        if (has && r0 + ty < r1) {
+            float sv[VE];
+            int so[VE];
+            int64_t r = r0 + ty;
+            {
+                E e[VE];
+                axis_load<VB, Ld>(x, slab + r * a.inner, e);
+#pragma unroll
+                for (int k = 0; k < VE; k++) {
+                    sv[k] = e[k];
+                    so[k] = (int)(r - r0);
+                }
+            }
+            r += ry;
+            for (; r + (int64_t)(U - 1) * ry < r1; r += (int64_t)U * ry) {
+                E e[U][VE];
+#pragma unroll
+                for (int u = 0; u < U; u++) axis_load<VB, Ld>(x, slab + (r + (int64_t)u * ry) * a.inner, e[u]);
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int rel = (int)(r + (int64_t)u * ry - r0);
+#pragma unroll
+                    for (int k = 0; k < VE; k++) {
+                        const float m = T::ordered_pick(sv[k], e[u][k]);
+                        so[k] = __float_as_uint(m) != __float_as_uint(sv[k]) ? rel : so[k];
+                        sv[k] = m;
+                    }
+                }
+            }
+            for (; r < r1; r += ry) {
+                E e[VE];
+                axis_load<VB, Ld>(x, slab + r * a.inner, e);
+                const int rel = (int)(r - r0);
+#pragma unroll
+                for (int k = 0; k < VE; k++) {
+                    const float m = T::ordered_pick(sv[k], e[k]);
+                    so[k] = __float_as_uint(m) != __float_as_uint(sv[k]) ? rel : so[k];
+                    sv[k] = m;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < VE; k++) acc[k] = T::from_ordered(sv[k], r0 + so[k]);
+        }
+    } else if (has) {
         int64_t r = r0 + ty;
         for (; r + (int64_t)(U - 1) * ry < r1; r += (int64_t)U * ry) {
             E e[U][VE];

@@ -627,6 +627,18 @@ struct ArgExtF {
         a.so = up ? i : a.so;
         a.sv = m;
     }
+    // The same in-order step on a caller's pair of registers (running
+    // extremum and its row, the pair started at the first element, so no
+    // test for "none yet"): k_axis keeps the row as a 32-bit offset and
+    // builds the accumulator once at the end.
+    static constexpr bool kOrderedPair = true;
+    __device__ __forceinline__ static float ordered_pick(float a, E v) { return MaxMinF<Ld_, OutK, MX>::f(a, v); }
+    __device__ __forceinline__ static Acc from_ordered(float sv, int64_t i) {
+        Acc a = init();
+        a.sv = sv;
+        a.so = i;
+        return a;
+    }
     template <int N>
     __device__ __forceinline__ static void add_vec(Acc& a, const E (&e)[N], int64_t i0) {
         static_assert(N <= kMaxN, "vector wider than the saved copy");
