@@ -9,19 +9,21 @@
 //     outside [x, x+n); the identity is never needed as a load mask).
 //   Step 3: the U accumulators are combined, then the warp (shuffle butterfly
 //     or redux.sync), then the block (one value per warp in shared memory).
-//   Large inputs (dyn): the grid-stride part stops at a multiple of the
-//     grid's stride near nine tenths of the vectors, and the rest is cut into
-//     tiles of blockDim x TL vectors that blocks claim from an atomic counter
-//     (the next claim issued while the current tile loads).  SMs stream at
-//     unequal rates (their finishing times spread over a few microseconds),
-//     so a static split ends when the slowest SM does; claimed tiles let the
-//     fast SMs take the slow ones' share of the end.  Each tile is reduced by
-//     its block like a block partial and stored in a slot indexed by the
-//     tile, so the result does not depend on which block took which tile.
+//   Large inputs (the TAIL variant): the grid-stride part stops at a
+//     multiple of the grid's stride near nine tenths of the vectors, and the
+//     rest is cut into tiles of whole rounds of blockDim x TL vectors (about
+//     128 KiB) that blocks claim from an atomic counter, a claim ahead.  SMs
+//     stream at unequal rates (their finishing times spread over a few
+//     microseconds), so a static split ends when the slowest SM does;
+//     claimed tiles let the fast SMs take the slow ones' share of the end.
+//     An exact trait adds the tiles to its accumulators; any other reduces
+//     each tile like a block partial, stored in a slot indexed by the tile,
+//     so the result does not depend on which block took which tile.
 //   Stage 2 (Section 2.3), fused: every block stores its partial; the last
 //     block to finish (atomic ticket after a fence) combines all partials in
 //     block-index order, then the tile partials in tile order, writes the
-//     result and re-arms the ticket and claim counters.
+//     result and re-arms the ticket and claim counters.  A launch of one
+//     block (small inputs) finishes with the same combine and no ticket.
 //
 // k_segmented  many reductions (segments of a CSR offsets array, or equal rows)
 //   in one launch.  The element range [offsets[0], offsets[nseg]) is cut into
