@@ -71,3 +71,15 @@ def test_sweep_sizes_span_the_configuration():
     sizes = bench.SWEEP_SIZES
     assert sizes[0] == 1 << 10 and max(sizes) == 1 << 30 and 5_533_214 in sizes
     assert all(1 << e in sizes for e in range(10, 31))
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The traffic record's hash reads the kernel sources' code: comments and
+    spacing do not change it, code and string literals do."""
+    src = 'int a = 1; // note\n/* block\n comment */ const char* s = "a//b /*x*/";\n'
+    code = bench._code_only(src)
+    assert code == 'int a = 1; const char* s = "a//b /*x*/";'
+    assert bench._code_only(src.replace("// note", "// another note")) == code
+    assert bench._code_only(src.replace("int a = 1;", "int   a = 1;")) == code
+    assert bench._code_only(src.replace("a = 1", "a = 2")) != code
+    assert len(bench.kernel_hash()) == 16
